@@ -1,0 +1,120 @@
+/*
+ * ppo.h -- ParPaRaw ORACLE (test infrastructure only).
+ *
+ * A plain, slow, obviously correct, sequential CPU restatement of what the
+ * ParPaRaw method computes (Stehle & Jacobsen, "ParPaRaw: Massively Parallel
+ * Parsing of Delimiter-Separated Raw Data"):
+ *
+ *   - a DFA over symbol groups drives the parse (Sec. 3.1, Table 1);
+ *   - the per-chunk state-transition vector and its composite operator
+ *     (Sec. 3.1) are given by their definitions, one DFA run per start state;
+ *   - the parse itself is ONE left-to-right Mealy pass: the method reaches
+ *     exactly the result of the sequential DFA run (Sec. 3.1), so the oracle
+ *     is that run written out, byte by byte, with a 256-entry group table;
+ *   - fields are gathered per column in record order (Sec. 3.3) into an
+ *     Arrow-like layout (Sec. 5, Apache Arrow output);
+ *   - type conversion (Sec. 3.3) uses the C library (strtoll, strtod, timegm)
+ *     as its definition.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline /
+ * reference legs may load or call this library.  It shares no code, header,
+ * table or helper with the CUDA path, and imports nothing from it.
+ */
+#ifndef PPO_H
+#define PPO_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPO_MAX_STATES 8
+#define PPO_MAX_GROUPS 16
+#define PPO_MAX_COLUMNS 64
+#define PPO_NO_STATE 0xFF
+#define PPO_NUMERIC_MAX_LEN 64
+
+/* per-byte tags: the paper's three bitmap indexes (record delimiter, field
+ * delimiter, control symbol) plus "part of the field" (Sec. 3.1). */
+enum { PPO_DATA = 0, PPO_FIELD = 1, PPO_RECORD = 2, PPO_CONTROL = 3 };
+
+enum {
+  PPO_STRING = 0,
+  PPO_INT32 = 1,
+  PPO_INT64 = 2,
+  PPO_FLOAT64 = 3,
+  PPO_TIMESTAMP_S = 4,  /* YYYY-MM-DD[ T]hh:mm:ss -> int64 seconds, UTC */
+  PPO_DATE_D = 5,       /* YYYY-MM-DD -> int32 days since 1970-01-01 */
+  PPO_TIMESTAMP_CLF = 6 /* dd/Mon/yyyy:hh:mm:ss +hhmm -> int64 seconds, UTC */
+};
+
+enum {
+  PPO_OK = 0,
+  PPO_E_INVALID_INPUT = -4,
+  PPO_E_UNTERMINATED = -5
+};
+
+/* conversion outcomes */
+enum { PPO_CONV_OK = 0, PPO_CONV_EMPTY = 1, PPO_CONV_FAIL = 2 };
+
+typedef struct ppo_format {
+  uint32_t num_states;                       /* S */
+  uint32_t num_groups;                       /* G */
+  uint8_t next[PPO_MAX_GROUPS][PPO_MAX_STATES]; /* transition table, one row per group */
+  uint8_t emit[PPO_MAX_GROUPS][PPO_MAX_STATES]; /* tag emitted by (group, state) */
+  uint8_t group_of[256];                     /* symbol -> group, catch-all elsewhere */
+  uint8_t start_state;
+  uint8_t invalid_state;                     /* PPO_NO_STATE if none */
+  uint32_t accept_mask;                      /* bit s: state s accepting at end */
+} ppo_format;
+
+typedef struct ppo_result {
+  int32_t status;
+  int32_t final_state;
+  int64_t rows;
+  int64_t n_rejected;
+  int64_t first_invalid_offset;              /* -1 if the input never enters INV */
+  uint32_t num_columns;
+  uint32_t types[PPO_MAX_COLUMNS];
+  /* STRING: values = bytes, offsets[rows+1]; others: values = rows fixed-width */
+  void* values[PPO_MAX_COLUMNS];
+  int64_t* offsets[PPO_MAX_COLUMNS];
+  uint8_t* validity[PPO_MAX_COLUMNS];        /* Arrow bitmaps, LSB first */
+  int64_t bytes_total[PPO_MAX_COLUMNS];      /* data bytes seen for a string column */
+  uint8_t* row_valid;
+} ppo_result;
+
+/* Build a format from a transition table next[g*S+s], tag table emit[g*S+s]
+ * and a symbol list; every byte not listed maps to catch_all. Returns 0 on
+ * success, -1 on a malformed table. */
+int ppo_format_init(ppo_format* f, uint32_t S, uint32_t G, const uint8_t* next,
+                    const uint8_t* emit, uint32_t nsym, const uint8_t* symbols,
+                    const uint8_t* groups, uint8_t catch_all, uint8_t start_state,
+                    uint8_t invalid_state, uint32_t accept_mask);
+
+/* Sec. 3.1: state-transition vector of a chunk. out[i] = state reached after
+ * reading the chunk when the DFA starts in state i (one DFA run per state). */
+void ppo_state_vector(const ppo_format* f, const uint8_t* chunk, size_t len,
+                      uint8_t out[PPO_MAX_STATES]);
+
+/* Sec. 3.1: composite of two state-transition vectors, (a o b)_i = b[a_i]. */
+void ppo_compose(uint32_t S, const uint8_t* a, const uint8_t* b, uint8_t* out);
+
+/* The sequential run: per byte, the tag emitted and the state entered. */
+void ppo_trace(const ppo_format* f, const uint8_t* in, size_t len, uint8_t* tags,
+               uint8_t* states_after);
+
+/* The full parse into Arrow-like columns (allocates; free with ppo_free). */
+int ppo_parse(const ppo_format* f, const uint32_t* types, uint32_t num_columns,
+              const uint8_t* in, size_t len, ppo_result* out);
+void ppo_free(ppo_result* r);
+
+/* Type conversion of one field's data bytes (Sec. 3.3). *out receives an
+ * int32/int64/double bit pattern in its low bytes. Returns PPO_CONV_*. */
+int ppo_convert(uint32_t type, const uint8_t* text, size_t len, void* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,303 @@
+"""Pins of the oracle to things other than itself.
+
+Each test ties a part of the oracle to what the paper prints (Table 1, the
+prefix-sum example of Sec. 2), to hand-worked examples, to algebraic facts of
+the method (the composite operator of Sec. 3.1 is associative and composing
+chunk vectors reproduces the sequential run for every split), to an
+independent format-specific rule (quote parity for RFC-4180 input) or to the
+C/Python standard libraries (conversion).
+"""
+import calendar
+import datetime as dt
+import itertools
+import json
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+NAMES = {"EOR": O.EOR, "ENC": O.ENC, "FLD": O.FLD, "EOF": O.EOF_, "ESC": O.ESC, "INV": O.INV}
+
+
+def test_csv_dfa_contains_table1():
+    """Table 1 (Sec. 4.5): the oracle's CSV DFA restricted to the groups
+    \\n, ", ',' and catch-all is the paper's transition table."""
+    f = O.csv6()
+    sym_to_group = {"\\n": f.group_of(ord("\n")), '"': f.group_of(ord('"')),
+                    ",": f.group_of(ord(",")), "*": f.group_of(ord("x"))}
+    rows = [l.split() for l in open(os.path.join(GOLD, "table1_csv_dfa.txt")) if not l.startswith("#")]
+    assert len(rows) == 4
+    for row in rows:
+        g = sym_to_group[row[1]]
+        assert [int(x) for x in f.next[g]] == [NAMES[s] for s in row[2:8]], row
+
+
+def test_state_vector_worked_example():
+    """The chunk '",' read from each start state EOR, ENC, FLD, EOF, ESC, INV
+    (worked by hand from Table 1) ends in ENC, EOF, INV, ENC, ENC, INV."""
+    v = O.state_vector(O.csv6(), b'",')
+    assert list(v) == [O.ENC, O.EOF_, O.INV, O.ENC, O.ENC, O.INV]
+
+
+def test_compose_order_and_identity():
+    # (a o b)_i = b[a_i]: a maps 0->1, b maps 1->2, so a o b maps 0->2
+    a = np.array([1, 1, 2], np.uint8)
+    b = np.array([0, 2, 0], np.uint8)
+    assert list(O.compose(a, b)) == [2, 2, 0]
+    assert list(O.compose(b, a)) == [1, 2, 1]
+    ident = np.arange(3, dtype=np.uint8)
+    assert list(O.compose(a, ident)) == list(a)
+    assert list(O.compose(ident, a)) == list(a)
+
+
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_compose_associative_exhaustive(S):
+    vecs = [np.array(v, np.uint8) for v in itertools.product(range(S), repeat=S)]
+    for a in vecs:
+        for b in vecs:
+            ab = O.compose(a, b)
+            for c in vecs:
+                assert np.array_equal(O.compose(ab, c), O.compose(a, O.compose(b, c)))
+
+
+@pytest.mark.parametrize("S", [6, 8])
+def test_compose_associative_random(S):
+    rng = np.random.default_rng(S)
+    for _ in range(2000):
+        a, b, c = (rng.integers(0, S, S).astype(np.uint8) for _ in range(3))
+        assert np.array_equal(O.compose(O.compose(a, b), c), O.compose(a, O.compose(b, c)))
+
+
+def _check_all_splits(fmt, s: bytes):
+    """Composing the vectors of the chunks of every split of s gives s's
+    vector, and its entry for the start state is the sequential end state."""
+    L = len(s)
+    sub = {(i, j): O.state_vector(fmt, s[i:j]) for i in range(L + 1) for j in range(i, L + 1)}
+    whole = sub[(0, L)]
+    for mask in range(1 << max(L - 1, 0)):
+        cuts = [0] + [k + 1 for k in range(L - 1) if mask >> k & 1] + [L]
+        acc = np.arange(fmt.num_states, dtype=np.uint8)
+        for i, j in zip(cuts, cuts[1:]):
+            acc = sub[(i, j)][acc]  # acc o chunk
+        assert np.array_equal(acc, whole), (s, cuts)
+    _, states = O.trace(fmt, s)
+    end = states[-1] if L else fmt.start_state
+    assert whole[fmt.start_state] == end
+
+
+def test_every_split_csv_exhaustive():
+    f = O.csv6()
+    for L in range(0, 6):
+        for t in itertools.product(b'\n,"\ra', repeat=L):
+            _check_all_splits(f, bytes(t))
+
+
+def test_every_split_log_random():
+    f = O.log8()
+    rng = random.Random(7)
+    for _ in range(300):
+        L = rng.randint(1, 8)
+        _check_all_splits(f, bytes(rng.choice(b'\n "[]a') for _ in range(L)))
+
+
+def test_random_splits_long_inputs():
+    f = O.csv6()
+    raw, _ = synth.records("mixed", 11, 0, 40)
+    rng = random.Random(3)
+    whole = O.state_vector(f, raw)
+    for _ in range(50):
+        cuts = sorted({0, len(raw), *rng.sample(range(1, len(raw)), 12)})
+        acc = np.arange(6, dtype=np.uint8)
+        for i, j in zip(cuts, cuts[1:]):
+            acc = O.state_vector(f, raw[i:j])[acc]
+        assert np.array_equal(acc, whole)
+
+
+def _status(name):
+    return {"ok": O.OK, "invalid": O.E_INVALID_INPUT, "unterminated": O.E_UNTERMINATED}[name]
+
+
+def test_worked_examples():
+    cases = json.load(open(os.path.join(GOLD, "worked_examples.json")))["cases"]
+    for case in cases:
+        fmt = O.csv6() if case["dialect"] == "csv" else O.log8()
+        data = case["input"].encode()
+        r = O.parse(fmt, [O.STRING] * case["columns"], data)
+        assert r.status == _status(case["status"]), case
+        if "first_invalid" in case:
+            assert r.first_invalid_offset == case["first_invalid"], case
+        else:
+            assert r.first_invalid_offset == -1
+        assert r.rows == len(case["rows"]), case
+        rejected = set(case.get("rejected", []))
+        assert r.n_rejected == len(rejected)
+        for i, row in enumerate(case["rows"]):
+            assert [r.field(i, c) for c in range(case["columns"])] == [x.encode() for x in row], case
+            for c in range(case["columns"]):
+                assert r.valid(i, c) == (i not in rejected)
+
+
+def test_prefix_sum_example_as_string_offsets():
+    """Sec. 2's prefix-sum example: fields of lengths 3 5 1 2 9 7 4 2 in one
+    string column give Arrow offsets equal to its exclusive sums plus the
+    total (the last inclusive sum)."""
+    lines = {l.split()[0]: [int(x) for x in l.split()[1:]]
+             for l in open(os.path.join(GOLD, "prefix_sum.txt")) if not l.startswith("#")}
+    data = b"".join(b"x" * n + b"\n" for n in lines["x"])
+    r = O.parse(O.csv6(), [O.STRING], data)
+    offs = list(r.columns[0].offsets)
+    assert offs[:-1] == lines["exclusive"]
+    assert offs[1:] == lines["inclusive"]
+
+
+def test_quote_parity_cross_check():
+    """For RFC-4180 input, a non-quote byte is inside an enclosed field iff an
+    odd number of double quotes precede it (the format-specific rule the
+    paper avoids, Sec. 2); the DFA context must agree with it."""
+    f = O.csv6()
+    raw, _ = synth.records("mixed", 5, 0, 400)
+    tags, states = O.trace(f, raw)
+    before = np.concatenate([[f.start_state], states[:-1]])
+    buf = np.frombuffer(raw, np.uint8)
+    quotes = np.cumsum(buf == ord('"')) - (buf == ord('"'))
+    nonq = buf != ord('"')
+    assert np.array_equal((before == O.ENC)[nonq], (quotes % 2 == 1)[nonq])
+
+
+# ----------------------------------------------------------- conversions
+
+def test_int_conversion_pins():
+    rng = random.Random(1)
+    for _ in range(3000):
+        v = rng.randint(-2**31, 2**31 - 1)
+        assert O.convert(O.INT32, str(v).encode()) == (O.CONV_OK, v)
+        w = rng.randint(-2**63, 2**63 - 1)
+        assert O.convert(O.INT64, str(w).encode()) == (O.CONV_OK, w)
+    for txt, ok in [(b"2147483647", True), (b"2147483648", False), (b"-2147483648", True),
+                    (b"-2147483649", False), (b"007", True), (b"-0", True), (b"+1", False),
+                    (b" 1", False), (b"1 ", False), (b"-", False), (b"1.0", False), (b"0x1", False)]:
+        st, v = O.convert(O.INT32, txt)
+        assert (st == O.CONV_OK) == ok, txt
+        if ok:
+            assert v == int(txt)
+    assert O.convert(O.INT64, b"9223372036854775807") == (O.CONV_OK, 2**63 - 1)
+    assert O.convert(O.INT64, b"9223372036854775808")[0] == O.CONV_FAIL
+    assert O.convert(O.INT64, b"-9223372036854775808") == (O.CONV_OK, -2**63)
+    assert O.convert(O.INT32, b"") == (O.CONV_EMPTY, 0)
+    assert O.convert(O.INT32, b"1" * 65)[0] == O.CONV_FAIL
+
+
+def test_float_conversion_matches_correct_rounding():
+    """Inside the accepted range the result equals Python's correctly rounded
+    decimal-to-double conversion."""
+    rng = random.Random(2)
+    for _ in range(20000):
+        frac = rng.randint(0, 22)
+        sig = rng.randint(1, 16)
+        m = rng.randrange(0, 2**53)
+        digits = str(m).rjust(frac + 1, "0")
+        txt = (("-" if rng.random() < 0.5 else "") + digits[: len(digits) - frac] +
+               ("." + digits[len(digits) - frac:] if frac else ""))
+        st, v = O.convert(O.FLOAT64, txt.encode())
+        assert st == O.CONV_OK, txt
+        ref = float(txt)
+        assert v == ref and math.copysign(1, v) == math.copysign(1, ref), txt
+        del sig
+    for txt, ok in [(b"1.", False), (b".5", False), (b"1e5", False), (b"-", False),
+                    (b"9007199254740991", True), (b"9007199254740992", False),
+                    (b"0." + b"0" * 21 + b"1", True), (b"0." + b"0" * 22 + b"1", False),
+                    (b"-0.00", True), (b"00012.50", True)]:
+        st, v = O.convert(O.FLOAT64, txt)
+        assert (st == O.CONV_OK) == ok, txt
+        if ok:
+            assert v == float(txt) and math.copysign(1, v) == math.copysign(1, float(txt))
+
+
+def test_date_and_timestamp_pins():
+    rng = random.Random(3)
+    epoch = dt.date(1970, 1, 1)
+    for _ in range(3000):
+        d = dt.date.fromordinal(rng.randint(dt.date(1, 1, 1).toordinal(), dt.date(9999, 12, 31).toordinal()))
+        assert O.convert(O.DATE_D, d.isoformat().encode()) == (O.CONV_OK, (d - epoch).days)
+        t = dt.datetime(d.year, d.month, d.day, rng.randint(0, 23), rng.randint(0, 59), rng.randint(0, 59))
+        secs = calendar.timegm(t.timetuple())
+        iso = f"{t.year:04d}-{t.month:02d}-{t.day:02d}T{t.hour:02d}:{t.minute:02d}:{t.second:02d}"
+        assert O.convert(O.TIMESTAMP_S, iso.encode()) == (O.CONV_OK, secs)
+        assert O.convert(O.TIMESTAMP_S, iso.replace("T", " ").encode()) == (O.CONV_OK, secs)
+        off = rng.randint(-23 * 60, 23 * 60)
+        tz = dt.timezone(dt.timedelta(minutes=off))
+        ta = t.replace(tzinfo=tz)
+        sign = "+" if off >= 0 else "-"
+        clf = (f"{t.day:02d}/{t.strftime('%b')}/{t.year:04d}:{t.hour:02d}:{t.minute:02d}:{t.second:02d} "
+               f"{sign}{abs(off) // 60:02d}{abs(off) % 60:02d}")
+        assert O.convert(O.TIMESTAMP_CLF, clf.encode()) == (O.CONV_OK, int(ta.timestamp()))
+    for bad in [b"2021-02-29", b"2020-13-01", b"2020-00-10", b"2020-01-32", b"0000-01-01", b"2020-1-01"]:
+        assert O.convert(O.DATE_D, bad)[0] == O.CONV_FAIL, bad
+    assert O.convert(O.DATE_D, b"2020-02-29")[0] == O.CONV_OK
+    for bad in [b"2020-01-01 24:00:00", b"2020-01-01 00:60:00", b"2020-01-01 00:00:60", b"2020-01-01X00:00:00"]:
+        assert O.convert(O.TIMESTAMP_S, bad)[0] == O.CONV_FAIL, bad
+    assert O.convert(O.TIMESTAMP_CLF, b"01/Foo/2020:00:00:00 +0000")[0] == O.CONV_FAIL
+
+
+# ------------------------------------------------------------- round trips
+
+_PYCONV = {
+    "int32": lambda t: int(t), "int64": lambda t: int(t), "float64": lambda t: float(t),
+    "timestamp": lambda t: calendar.timegm(dt.datetime.strptime(t.decode().replace("T", " "),
+                                                                "%Y-%m-%d %H:%M:%S").timetuple()),
+    "date": lambda t: (dt.date.fromisoformat(t.decode()) - dt.date(1970, 1, 1)).days,
+    "timestamp_clf": lambda t: int(dt.datetime.strptime(t.decode(), "%d/%b/%Y:%H:%M:%S %z").timestamp()),
+}
+_OTYPE = {"string": O.STRING, "int32": O.INT32, "int64": O.INT64, "float64": O.FLOAT64,
+          "timestamp": O.TIMESTAMP_S, "date": O.DATE_D, "timestamp_clf": O.TIMESTAMP_CLF}
+
+
+@pytest.mark.parametrize("workload,n", [("mixed", 3000), ("trip", 1500), ("review", 150), ("log", 2000)])
+def test_generator_round_trip(workload, n):
+    """The generator knows every field it wrote; the oracle's parse must give
+    back exactly those rows, fields and (through Python's own conversions)
+    values."""
+    raw, truth = synth.records(workload, synth.BASE_SEED + 99, 0, n)
+    schema = synth.SCHEMAS[workload]
+    fmt = O.csv6() if synth.DIALECT[workload] == "csv" else O.log8()
+    r = O.parse(fmt, [_OTYPE[t] for t in schema], raw)
+    assert r.status == O.OK and r.rows == n and r.n_rejected == 0
+    for i, rec in enumerate(truth):
+        assert len(rec) == len(schema)
+        for c, (t, txt) in enumerate(zip(schema, rec)):
+            if t == "string":
+                assert r.field(i, c) == txt
+                assert r.valid(i, c)
+            elif txt == b"":
+                assert not r.valid(i, c) and r.field(i, c) == 0
+            else:
+                assert r.valid(i, c)
+                assert r.field(i, c) == _PYCONV[t](txt), (i, c, txt)
+
+
+def test_rejects_and_nulls():
+    f = O.csv6()
+    types = [O.INT32, O.STRING, O.FLOAT64]
+    r = O.parse(f, types, b"1,a,2.5\n,b,\nx,c,1\n4,d\n5,e,6,7\n")
+    assert r.rows == 5 and r.n_rejected == 3
+    # row 0 valid; row 1 valid with two null numerics
+    assert [r.valid(0, c) for c in range(3)] == [True] * 3
+    assert [r.valid(1, c) for c in range(3)] == [False, True, False] and (r.row_valid[0] >> 1) & 1
+    # row 2: 'x' fails int32 -> rejected; its float still holds its value
+    assert not any(r.valid(2, c) for c in range(3)) and r.field(2, 2) == 1.0 and r.field(2, 0) == 0
+    # row 3: too few fields; row 4: too many (extra field dropped)
+    assert r.field(3, 0) == 4 and r.field(3, 1) == b"d" and r.field(3, 2) == 0.0
+    assert r.field(4, 0) == 5 and r.field(4, 2) == 6.0
+    assert [(r.row_valid[0] >> k) & 1 for k in range(5)] == [1, 1, 0, 0, 0]
+
+
+def test_bytes_total_counts_dropped_partial_record():
+    r = O.parse(O.csv6(), [O.STRING, O.STRING], b'ab,c\nde,"f')
+    assert r.status == O.E_UNTERMINATED and r.rows == 1
+    assert r.columns[0].bytes_total == 4 and r.columns[1].bytes_total == 2
