@@ -1,0 +1,242 @@
+/*
+ * parparaw.h -- C ABI of the GB300 ParPaRaw parser.
+ *
+ * ParPaRaw (Stehle & Jacobsen, "ParPaRaw: Massively Parallel Parsing of
+ * Delimiter-Separated Raw Data") parses delimiter-separated bytes on the GPU
+ * without a sequential pre-pass: every chunk is simulated from every DFA
+ * state at once (Sec. 3.1), the chunks' state-transition vectors are combined
+ * by an exclusive scan with the composite operator (Sec. 3.1), each chunk is
+ * simulated again from its now known state to tag symbols, records and
+ * column offsets are scanned (Sec. 3.2), and field bytes are gathered into
+ * per-column buffers and converted to the column type (Sec. 3.3).  The
+ * output follows the Apache Arrow columnar layout (Sec. 5).
+ *
+ * Conventions for every entry point:
+ *   - Plain pointers and sizes only.  "device" pointers are CUDA device
+ *     memory of the current device; "host" pointers are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - No exception ever crosses the ABI.  The return value reports argument,
+ *     allocation and launch errors; the outcome of a parse is written, on the
+ *     stream, into the caller's device-side pp_parse_result.
+ *   - Every device-side wait inside the kernels is bounded: if a wait expires,
+ *     the parse returns PP_E_TIMEOUT in its result instead of hanging.
+ */
+#ifndef PARPARAW_H
+#define PARPARAW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PP_MAX_STATES 8          /* |S| of a DFA */
+#define PP_MAX_GROUPS 16         /* symbol groups, catch-all included */
+#define PP_MAX_SYMBOLS 16        /* distinct byte values outside the catch-all */
+#define PP_MAX_COLUMNS 64        /* columns of a schema */
+#define PP_MAX_STRING_COLUMNS 16 /* STRING columns of a schema */
+#define PP_NO_STATE 0xFF
+
+typedef enum pp_status {
+  PP_OK = 0,
+  PP_E_ARG = -1,           /* a NULL or out-of-range argument */
+  PP_E_NOMEM = -2,         /* a device or host allocation failed */
+  PP_E_CUDA = -3,          /* a CUDA runtime call or launch failed */
+  PP_E_INVALID_INPUT = -4, /* the input entered the DFA's invalid state */
+  PP_E_UNTERMINATED = -5,  /* the input ended in a non-accepting state */
+  PP_E_CAPACITY = -6,      /* an output buffer is too small; sizes reported */
+  PP_E_TIMEOUT = -7,       /* a bounded device-side wait expired */
+  PP_E_BAD_TABLE = -8,     /* the DFA / symbol groups / schema are malformed */
+  PP_E_UNSUPPORTED = -9    /* a limit of this build was exceeded */
+} pp_status;
+
+/* Per-symbol tags: the paper's three bitmap indexes (record delimiter, field
+ * delimiter, control symbol) plus "part of a field value" (Sec. 3.1). */
+typedef enum pp_tag {
+  PP_TAG_DATA = 0,
+  PP_TAG_FIELD = 1,
+  PP_TAG_RECORD = 2,
+  PP_TAG_CONTROL = 3
+} pp_tag;
+
+/* Column types (Sec. 3.3 type conversion).  Numeric text longer than 64 data
+ * bytes, or that does not follow the syntax below, fails to convert and
+ * rejects its record.
+ *   PP_STRING        bytes, int64 offsets (Arrow LargeUtf8 layout)
+ *   PP_INT32         -?[0-9]+, must fit int32
+ *   PP_INT64         -?[0-9]+, must fit int64
+ *   PP_FLOAT64       -?[0-9]+(\.[0-9]+)?, decimal significand < 2^53 and at
+ *                    most 22 fraction digits; correctly rounded
+ *   PP_TIMESTAMP_S   YYYY-MM-DD hh:mm:ss or YYYY-MM-DDThh:mm:ss -> int64
+ *                    seconds since 1970-01-01 UTC (proleptic Gregorian)
+ *   PP_DATE_D        YYYY-MM-DD -> int32 days since 1970-01-01
+ *   PP_TIMESTAMP_CLF dd/Mon/yyyy:hh:mm:ss +hhmm (Common Log Format) -> int64
+ *                    seconds, UTC */
+typedef enum pp_type {
+  PP_STRING = 0,
+  PP_INT32 = 1,
+  PP_INT64 = 2,
+  PP_FLOAT64 = 3,
+  PP_TIMESTAMP_S = 4,
+  PP_DATE_D = 5,
+  PP_TIMESTAMP_CLF = 6
+} pp_type;
+
+/* DFA of the format (Sec. 3.1; Sec. 4.5, Table 1: one row of transitions per
+ * symbol group).  All pointers are host memory, read during create only.
+ *   transitions[g * num_states + s]  next state after a symbol of group g
+ *                                    read in state s
+ *   emit[g * num_states + s]         pp_tag of that symbol (Mealy output)
+ *   invalid_state                    absorbing error state, or PP_NO_STATE;
+ *                                    entering it is reported (Sec. 4.3)
+ *   accept_mask                      bit s set: input may end in state s */
+typedef struct pp_dfa {
+  uint32_t num_states; /* 1..PP_MAX_STATES */
+  uint32_t num_groups; /* 1..PP_MAX_GROUPS */
+  const uint8_t* transitions;
+  const uint8_t* emit;
+  uint8_t start_state;
+  uint8_t invalid_state;
+  uint32_t accept_mask;
+} pp_dfa;
+
+/* Symbol groups (Sec. 4.5): symbols with identical transitions share a group;
+ * every byte value not listed maps to `catch_all`.  Host memory. */
+typedef struct pp_symbol_groups {
+  uint32_t num_symbols;   /* 0..PP_MAX_SYMBOLS */
+  const uint8_t* symbols; /* distinct byte values */
+  const uint8_t* groups;  /* group of each symbol */
+  uint8_t catch_all;
+} pp_symbol_groups;
+
+/* Schema: one pp_type per column, host memory. */
+typedef struct pp_schema {
+  uint32_t num_columns; /* 1..PP_MAX_COLUMNS */
+  const uint32_t* types;
+} pp_schema;
+
+/* One output column, all device memory owned by the caller.
+ *   values    STRING: uint8_t[values_cap]; INT32/DATE_D: int32_t[rows_cap];
+ *             INT64/TIMESTAMP_*: int64_t[rows_cap]; FLOAT64: double[rows_cap]
+ *   offsets   STRING only: int64_t[rows_cap + 1]; NULL otherwise
+ *   validity  Arrow bitmap, LSB first, (rows_cap + 7) / 8 bytes
+ * Null slots: a numeric slot holds the value of its field text when that text
+ * converts and 0 otherwise; a string slot spans the bytes of its field if the
+ * field was present, also in a rejected row. */
+typedef struct pp_column {
+  void* values;
+  int64_t* offsets;
+  uint8_t* validity;
+  uint64_t values_cap; /* STRING: bytes available in values; else ignored */
+} pp_column;
+
+/* Outcome of one parse, written by the device at the end of the parse.
+ *   status               PP_OK or one of PP_E_INVALID_INPUT,
+ *                        PP_E_UNTERMINATED, PP_E_CAPACITY, PP_E_TIMEOUT
+ *                        (precedence: TIMEOUT, CAPACITY, INVALID, UNTERMINATED)
+ *   rows                 records emitted (rows needed on PP_E_CAPACITY)
+ *   n_rejected           records kept as all-null rows (field count differs
+ *                        from the schema, or a numeric field did not convert)
+ *   first_invalid_offset first byte whose transition enters the invalid
+ *                        state, or -1
+ *   values_bytes_needed  per STRING column, data bytes the input holds for it
+ *                        (the values_cap that is enough), else 0 */
+typedef struct pp_parse_result {
+  int32_t status;
+  int32_t final_state;
+  int64_t rows;
+  int64_t n_rejected;
+  int64_t first_invalid_offset;
+  int64_t values_bytes_needed[PP_MAX_COLUMNS];
+} pp_parse_result;
+
+/* Output descriptor (host struct holding device pointers).  On
+ * PP_E_CAPACITY nothing is written beyond any capacity and the result holds
+ * the sizes needed for a retry.  Rows before an invalid byte are output as
+ * usual; the record in progress at the end of an invalid or unterminated
+ * input is not emitted. */
+typedef struct pp_columns {
+  uint32_t num_columns;           /* must equal the schema's */
+  uint64_t rows_cap;
+  pp_column cols[PP_MAX_COLUMNS];
+  uint8_t* row_valid;             /* device bitmap, (rows_cap + 7) / 8 bytes */
+  pp_parse_result* result;        /* device memory */
+} pp_columns;
+
+typedef struct pp_parser pp_parser;
+
+/* Tuning options (parparaw_set_option). */
+typedef enum pp_option {
+  PP_OPT_TILE_CONFIG = 1,   /* 0 = default tile; 1 = 512-byte test tile;
+                               2 = 3 KiB tile; 3 = 28 KiB tile */
+  PP_OPT_TIMEOUT_MS = 2,    /* bound of every device-side wait (default 2000) */
+  PP_OPT_GRID_LIMIT = 3     /* 0 = one block per tile; n = at most n resident
+                               blocks looping over tiles (persistent) */
+} pp_option;
+
+typedef struct pp_parser_info {
+  uint32_t num_states, num_groups, num_symbols, num_columns, num_string_columns;
+  uint32_t catch_all_idempotent; /* runs of catch-all symbols collapse */
+  uint32_t tile_bytes;           /* input bytes per tile of the current config */
+  uint32_t threads_per_block;
+} pp_parser_info;
+
+/* Validates and copies the tables (Sec. 3.1 DFA, Sec. 4.5 symbol groups,
+ * schema).  Returns PP_E_BAD_TABLE when an entry is out of range, the invalid
+ * state is not absorbing, a symbol is listed twice or maps to the catch-all
+ * group, or the schema has an unknown type; PP_E_UNSUPPORTED when a limit of
+ * this header is exceeded.  Allocates no device memory.  The parser is
+ * immutable after its options are set and may be shared across host threads
+ * and streams.  *out is owned by the caller and released with
+ * parparaw_destroy. */
+pp_status parparaw_create(const pp_dfa* dfa, const pp_symbol_groups* groups,
+                          const pp_schema* schema, pp_parser** out);
+
+void parparaw_destroy(pp_parser* parser);
+
+pp_status parparaw_set_option(pp_parser* parser, pp_option option, int64_t value);
+
+pp_status parparaw_get_info(const pp_parser* parser, pp_parser_info* info);
+
+/* Parses `len` bytes at device address `input` into `out` (Sec. 3, whole
+ * pipeline), asynchronously on `stream`.  `input` and the buffers of `out`
+ * are caller-owned device memory and must stay valid until the stream has
+ * passed the parse; `out` itself (a host struct) is read before the call
+ * returns.  The library allocates its own scratch (tile status words, fail
+ * bitmaps) stream-ordered on `stream` and releases it the same way.  Returns
+ * PP_E_ARG / PP_E_NOMEM / PP_E_CUDA for errors detected on the host; the parse
+ * outcome is in out->result once the stream reaches it. */
+pp_status parparaw_parse(const pp_parser* parser, const uint8_t* input, uint64_t len,
+                         const pp_columns* out, void* stream);
+
+/* One item of a batch: its own parser (DFA, symbol groups, schema), input
+ * (device) and output descriptor (host struct holding device pointers). */
+typedef struct pp_batch_item {
+  const pp_parser* parser;
+  const uint8_t* input;
+  uint64_t len;
+  const pp_columns* out;
+} pp_batch_item;
+
+/* Parses `n` independent inputs, possibly with different parsers, in one
+ * persistent launch whose blocks take (input, tile) work items from a device
+ * queue; each input keeps its own look-back chains.  Every item's result is
+ * identical to its plain parparaw_parse.  `items` is host memory read before
+ * the call returns.  The tile configuration of the batch is that of the first
+ * item's parser. */
+pp_status parparaw_parse_batch(const pp_batch_item* items, uint64_t n, void* stream);
+
+/* Records the two CUDA events (cudaEvent_t passed as void*) on the stream
+ * immediately before and after the main parse kernel of every later parse or
+ * batch made with this parser, so that a caller can time that kernel alone.
+ * Pass NULL, NULL to stop. */
+pp_status parparaw_set_kernel_events(pp_parser* parser, void* start_event, void* stop_event);
+
+/* Static text for a pp_status value; never NULL. */
+const char* parparaw_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARPARAW_H */

@@ -1,0 +1,607 @@
+// pp_host.cu -- C ABI of the GB300 ParPaRaw parser (declared in
+// include/parparaw.h): table validation, scratch management, the init and
+// finalize kernels, and the launch of the tile kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "pp_device.cuh"
+#include "pp_launch.h"
+#include "pp_types.h"
+
+struct pp_parser {
+  pp::Tables tab;
+  uint32_t types[PP_MAX_COLUMNS];
+  int tile_config = 0;
+  uint64_t timeout_ns = 2000000000ull;
+  int64_t grid_limit = 0;
+  cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+};
+
+namespace pp {
+namespace {
+
+constexpr uint32_t kBlockInit = 256;
+constexpr uint32_t kBlockFinal = 256;
+
+// --------------------------------------------------------- init kernel ---
+// Zeroes every job's look-back flags, fail / null bitmaps and bookkeeping.
+__global__ void pp_init_kernel(const __grid_constant__ Launch L) {
+  for (uint32_t j = blockIdx.y; j < L.njobs; j += gridDim.y) {
+    const Job& J = L.jobs ? L.jobs[j] : L.job0;
+    const Tables& TB = L.jobs ? L.tables[J.tables] : L.tables0;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    const uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (uint64_t i = i0; i < J.ntiles; i += stride) {
+      J.st_state[i] = 0;
+      J.st_rc[i] = 0;
+      J.st_bytes_flag[i] = 0;
+    }
+    const uint64_t nbits = J.bit_words * (1 + static_cast<uint64_t>(TB.num_num));
+    for (uint64_t i = i0; i < nbits; i += stride) {
+      if (i < J.bit_words) J.fail_bits[i] = 0;
+      else J.null_bits[i - J.bit_words] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      Misc* M = J.misc;
+      M->first_invalid = ~0ull;
+      M->timeout = 0;
+      M->done = 0;
+      M->rows = 0;
+      M->final_state = TB.start_state;
+      for (int k = 0; k < PP_MAX_STRING_COLUMNS; ++k) M->bytes_total[k] = 0;
+      J.result->n_rejected = 0;
+    }
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *L.work_counter = 0ull;
+}
+
+__device__ __forceinline__ void put_bitmap_word(uint8_t* bm, uint64_t w, uint32_t bits, uint64_t nbytes) {
+  for (int k = 0; k < 4; ++k) {
+    const uint64_t b = 4 * w + k;
+    if (b < nbytes) bm[b] = static_cast<uint8_t>(bits >> (8 * k));
+  }
+}
+
+// ----------------------------------------------------- finalize kernel ---
+// Turns the fail / null bitmaps into Arrow validity bitmaps and row_valid,
+// counts rejected rows and writes the result of every job.
+__global__ void pp_finalize_kernel(const __grid_constant__ Launch L) {
+  __shared__ unsigned long long s_rej;
+  for (uint32_t j = blockIdx.y; j < L.njobs; j += gridDim.y) {
+    const Job& J = L.jobs ? L.jobs[j] : L.job0;
+    const Tables& TB = L.jobs ? L.tables[J.tables] : L.tables0;
+    const Col* cols = L.jobs ? (L.cols + J.col0) : L.cols0;
+    const Misc& M = *J.misc;
+    const bool ok_run = (J.ntiles == 0) || M.done;
+    const int64_t R = ok_run ? M.rows : 0;
+    const uint64_t rows_out = min(static_cast<uint64_t>(R), J.rows_cap);
+    const uint64_t words = (rows_out + 31) / 32;
+    const uint64_t nbytes = (rows_out + 7) / 8;
+    if (threadIdx.x == 0) s_rej = 0;
+    __syncthreads();
+    unsigned long long rej = 0;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t w = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; w < words; w += stride) {
+      const uint32_t live = (w + 1 == words && (rows_out & 31)) ? ((1u << (rows_out & 31)) - 1u) : ~0u;
+      const uint32_t fail = J.fail_bits[w] & live;
+      const uint32_t ok = ~fail & live;
+      rej += __popc(fail);
+      put_bitmap_word(J.row_valid, w, ok, nbytes);
+      for (uint32_t c = 0; c < TB.num_columns; ++c) {
+        uint32_t bits = ok;
+        if (TB.num_slot[c] != 0xFF) bits &= ~J.null_bits[TB.num_slot[c] * J.bit_words + w];
+        put_bitmap_word(cols[c].validity, w, bits, nbytes);
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) rej += __shfl_xor_sync(0xffffffffu, rej, off);
+    if ((threadIdx.x & 31) == 0 && rej) atomicAdd(&s_rej, rej);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_rej) atomicAdd(reinterpret_cast<unsigned long long*>(&J.result->n_rejected), s_rej);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      pp_parse_result* res = J.result;
+      int32_t status = PP_OK;
+      bool cap = static_cast<uint64_t>(R) > J.rows_cap;
+      for (uint32_t c = 0; c < TB.num_columns; ++c) {
+        const uint32_t slot = TB.str_slot[c];
+        const int64_t need = slot != 0xFF ? M.bytes_total[slot] : 0;
+        res->values_bytes_needed[c] = need;
+        if (slot != 0xFF) {
+          cols[c].offsets[0] = 0;
+          if (static_cast<uint64_t>(need) > cols[c].values_cap) cap = true;
+        }
+      }
+      for (uint32_t c = TB.num_columns; c < PP_MAX_COLUMNS; ++c) res->values_bytes_needed[c] = 0;
+      if (M.timeout || !ok_run) status = PP_E_TIMEOUT;
+      else if (cap) status = PP_E_CAPACITY;
+      else if (M.first_invalid != ~0ull) status = PP_E_INVALID_INPUT;
+      else if (!((TB.accept_mask >> M.final_state) & 1u)) status = PP_E_UNTERMINATED;
+      res->status = status;
+      res->final_state = M.final_state;
+      res->rows = R;
+      res->first_invalid_offset = M.first_invalid == ~0ull ? -1 : static_cast<int64_t>(M.first_invalid);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ device caches ---
+
+struct KernelSlot {
+  std::once_flag once;
+  int blocks_per_sm = 0;
+  cudaError_t err = cudaSuccess;
+};
+
+std::mutex g_mu;
+
+ShapeInfo shape_for(int cfg) {
+  switch (cfg) {
+    case 1: return shape_info_tiny();
+    case 2: return shape_info_small();
+    case 3: return shape_info_mid();
+    case 4: return shape_info_wide();
+    default: return shape_info_mid();
+  }
+}
+
+struct DeviceProps {
+  int sms = 0;
+};
+
+cudaError_t device_props(int dev, DeviceProps* out) {
+  static std::unordered_map<int, DeviceProps> cache;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  DeviceProps p;
+  cudaError_t e = cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  cache[dev] = p;
+  *out = p;
+  return cudaSuccess;
+}
+
+// resident blocks per SM of one kernel on one device (sets the shared-memory
+// attribute the first time)
+cudaError_t kernel_occupancy(const void* kernel, int threads, size_t smem, int dev, int* out) {
+  static std::unordered_map<const void*, std::unordered_map<int, int>> cache;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = cache.find(kernel);
+    if (it != cache.end()) {
+      auto jt = it->second.find(dev);
+      if (jt != it->second.end()) {
+        *out = jt->second;
+        return cudaSuccess;
+      }
+    }
+  }
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int n = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (n < 1) return cudaErrorInvalidConfiguration;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cache[kernel][dev] = n;
+  *out = n;
+  return cudaSuccess;
+}
+
+int nspec_of(const Tables& t) { return t.num_symbols <= 4 ? 4 : (t.num_symbols <= 8 ? 8 : 16); }
+
+bool column_ok(const pp_column& c, uint32_t type) {
+  if (c.validity == nullptr || c.values == nullptr) return false;
+  if (type == PP_STRING) return c.offsets != nullptr;
+  return true;
+}
+
+// Scratch of one job, carved from one stream-ordered allocation.
+struct ScratchPlan {
+  size_t st_state, st_rc, st_flag, st_agg, st_inc, fail, null_, misc, total;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+ScratchPlan plan_scratch(size_t base, uint64_t ntiles, uint32_t ns, uint32_t nn, uint64_t bit_words) {
+  ScratchPlan p;
+  size_t o = align_up(base, 256);
+  p.misc = o; o = align_up(o + sizeof(Misc), 256);
+  p.st_state = o; o = align_up(o + 8 * ntiles, 256);
+  p.st_rc = o; o = align_up(o + 8 * ntiles, 256);
+  p.st_flag = o; o = align_up(o + 4 * ntiles, 256);
+  p.st_agg = o; o = align_up(o + 8 * ntiles * ns, 256);
+  p.st_inc = o; o = align_up(o + 8 * ntiles * ns, 256);
+  p.fail = o; o = align_up(o + 4 * bit_words, 256);
+  p.null_ = o; o = align_up(o + 4 * bit_words * nn, 256);
+  p.total = o;
+  return p;
+}
+
+void fill_job(Job& J, const ScratchPlan& p, uint8_t* scratch) {
+  J.misc = reinterpret_cast<Misc*>(scratch + p.misc);
+  J.st_state = reinterpret_cast<uint64_t*>(scratch + p.st_state);
+  J.st_rc = reinterpret_cast<uint64_t*>(scratch + p.st_rc);
+  J.st_bytes_flag = reinterpret_cast<uint32_t*>(scratch + p.st_flag);
+  J.st_bytes_agg = reinterpret_cast<int64_t*>(scratch + p.st_agg);
+  J.st_bytes_inc = reinterpret_cast<int64_t*>(scratch + p.st_inc);
+  J.fail_bits = reinterpret_cast<uint32_t*>(scratch + p.fail);
+  J.null_bits = reinterpret_cast<uint32_t*>(scratch + p.null_);
+}
+
+pp_status check_columns(const pp_parser* P, const pp_columns* out) {
+  if (out == nullptr || out->result == nullptr || out->row_valid == nullptr) return PP_E_ARG;
+  if (out->num_columns != P->tab.num_columns) return PP_E_ARG;
+  for (uint32_t c = 0; c < out->num_columns; ++c)
+    if (!column_ok(out->cols[c], P->types[c])) return PP_E_ARG;
+  return PP_OK;
+}
+
+pp_status map_err(cudaError_t e) {
+  if (e == cudaSuccess) return PP_OK;
+  if (e == cudaErrorMemoryAllocation) return PP_E_NOMEM;
+  return PP_E_CUDA;
+}
+
+// Launches init, tile and finalize kernels for a prepared launch.
+pp_status run_launch(Launch& L, const ShapeInfo& shape, int nspec, int64_t grid_limit,
+                     const pp_parser* timing, cudaStream_t stream, uint32_t max_jobs_y,
+                     uint64_t max_tiles, uint64_t max_words) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return map_err(e);
+  DeviceProps props;
+  if ((e = device_props(dev, &props)) != cudaSuccess) return map_err(e);
+
+  const uint32_t gy = std::max<uint32_t>(1, std::min<uint32_t>(max_jobs_y, 65535));
+  const uint32_t gx_init = static_cast<uint32_t>(
+      std::max<uint64_t>(1, std::min<uint64_t>((std::max(max_tiles, max_words) + kBlockInit - 1) / kBlockInit, 1024)));
+  pp_init_kernel<<<dim3(gx_init, gy), kBlockInit, 0, stream>>>(L);
+  if ((e = cudaGetLastError()) != cudaSuccess) return map_err(e);
+
+  if (L.total_tiles > 0) {
+    const void* kern = shape.kernel(nspec);
+    int per_sm = 0;
+    if ((e = kernel_occupancy(kern, shape.threads, shape.smem_bytes, dev, &per_sm)) != cudaSuccess)
+      return map_err(e);
+    uint64_t grid = std::min<uint64_t>(L.total_tiles, static_cast<uint64_t>(per_sm) * props.sms);
+    if (grid_limit > 0) grid = std::min<uint64_t>(grid, static_cast<uint64_t>(grid_limit));
+    if (timing && timing->ev_start) cudaEventRecord(timing->ev_start, stream);
+    void* args[] = {&L};
+    e = cudaLaunchKernel(kern, dim3(static_cast<uint32_t>(grid)), dim3(shape.threads), args,
+                         shape.smem_bytes, stream);
+    if (e != cudaSuccess) return map_err(e);
+    if (timing && timing->ev_stop) cudaEventRecord(timing->ev_stop, stream);
+  }
+
+  const uint32_t gx_fin = static_cast<uint32_t>(
+      std::max<uint64_t>(1, std::min<uint64_t>((max_words + kBlockFinal - 1) / kBlockFinal, 1024)));
+  pp_finalize_kernel<<<dim3(gx_fin, gy), kBlockFinal, 0, stream>>>(L);
+  if ((e = cudaGetLastError()) != cudaSuccess) return map_err(e);
+  return PP_OK;
+}
+
+}  // namespace
+}  // namespace pp
+
+using namespace pp;
+
+// ============================================================== the ABI ===
+
+extern "C" const char* parparaw_status_string(int status) {
+  switch (status) {
+    case PP_OK: return "ok";
+    case PP_E_ARG: return "invalid argument";
+    case PP_E_NOMEM: return "out of memory";
+    case PP_E_CUDA: return "CUDA error";
+    case PP_E_INVALID_INPUT: return "input entered the invalid state";
+    case PP_E_UNTERMINATED: return "input ended in a non-accepting state";
+    case PP_E_CAPACITY: return "output capacity exceeded";
+    case PP_E_TIMEOUT: return "device wait timed out";
+    case PP_E_BAD_TABLE: return "malformed DFA, symbol groups or schema";
+    case PP_E_UNSUPPORTED: return "limit of this build exceeded";
+    default: return "unknown status";
+  }
+}
+
+extern "C" pp_status parparaw_create(const pp_dfa* dfa, const pp_symbol_groups* groups,
+                                     const pp_schema* schema, pp_parser** out) {
+  if (out == nullptr) return PP_E_ARG;
+  *out = nullptr;
+  if (dfa == nullptr || groups == nullptr || schema == nullptr) return PP_E_ARG;
+  if (dfa->transitions == nullptr || dfa->emit == nullptr) return PP_E_ARG;
+  const uint32_t S = dfa->num_states, G = dfa->num_groups;
+  if (S == 0 || G == 0) return PP_E_BAD_TABLE;
+  if (S > PP_MAX_STATES || G > PP_MAX_GROUPS) return PP_E_UNSUPPORTED;
+  if (dfa->start_state >= S) return PP_E_BAD_TABLE;
+  if (dfa->invalid_state != PP_NO_STATE && dfa->invalid_state >= S) return PP_E_BAD_TABLE;
+  if (groups->catch_all >= G) return PP_E_BAD_TABLE;
+  if (groups->num_symbols > PP_MAX_SYMBOLS) return PP_E_UNSUPPORTED;
+  if (groups->num_symbols > 0 && (groups->symbols == nullptr || groups->groups == nullptr)) return PP_E_ARG;
+  if (schema->num_columns == 0 || schema->types == nullptr) return PP_E_BAD_TABLE;
+  if (schema->num_columns > PP_MAX_COLUMNS) return PP_E_UNSUPPORTED;
+
+  pp_parser* P = new (std::nothrow) pp_parser();
+  if (P == nullptr) return PP_E_NOMEM;
+  Tables& T = P->tab;
+  std::memset(&T, 0, sizeof(T));
+  for (uint32_t g = 0; g < G; ++g) {
+    uint64_t row = 0;
+    uint32_t em = 0;
+    for (uint32_t s = 0; s < PP_MAX_STATES; ++s) {
+      uint32_t nxt = s, tag = PP_TAG_CONTROL;
+      if (s < S) {
+        nxt = dfa->transitions[g * S + s];
+        tag = dfa->emit[g * S + s];
+        if (nxt >= S || tag > PP_TAG_CONTROL) { delete P; return PP_E_BAD_TABLE; }
+      }
+      row |= static_cast<uint64_t>(nxt) << (8 * s);
+      em |= tag << (2 * s);
+    }
+    T.trans[g] = row;
+    T.emit[g] = em;
+  }
+  if (dfa->invalid_state != PP_NO_STATE) {
+    const uint32_t inv = dfa->invalid_state;
+    for (uint32_t g = 0; g < G; ++g) {
+      if (((T.trans[g] >> (8 * inv)) & 0xFF) != inv || ((T.emit[g] >> (2 * inv)) & 3u) != PP_TAG_CONTROL) {
+        delete P;
+        return PP_E_BAD_TABLE;  // the invalid state must absorb and emit nothing
+      }
+    }
+  }
+  bool seen[256] = {false};
+  for (int b = 0; b < 256; ++b) T.group_of[b] = groups->catch_all;
+  for (uint32_t i = 0; i < groups->num_symbols; ++i) {
+    const uint8_t b = groups->symbols[i], g = groups->groups[i];
+    if (seen[b] || g >= G || g == groups->catch_all) { delete P; return PP_E_BAD_TABLE; }
+    seen[b] = true;
+    T.group_of[b] = g;
+    T.rep[i] = 0x01010101u * b;
+  }
+  // composite of a catch-all run followed by each group: (T_* o T_g)_i = T_g[T_*[i]]
+  const uint64_t tca = T.trans[groups->catch_all];
+  for (uint32_t g = 0; g < PP_MAX_GROUPS; ++g) {
+    uint64_t row = 0;
+    for (uint32_t s = 0; s < PP_MAX_STATES; ++s) {
+      const uint32_t mid = (tca >> (8 * s)) & 0xFF;
+      row |= ((T.trans[g] >> (8 * mid)) & 0xFFull) << (8 * s);
+    }
+    T.trans_run[g] = row;
+  }
+  bool idem = true;
+  for (uint32_t s = 0; s < S; ++s) {
+    const uint32_t once = (tca >> (8 * s)) & 0xFF;
+    if (((tca >> (8 * once)) & 0xFF) != once) idem = false;
+  }
+  T.idempotent = idem ? 1 : 0;
+  T.num_states = static_cast<uint8_t>(S);
+  T.num_groups = static_cast<uint8_t>(G);
+  T.num_symbols = static_cast<uint8_t>(groups->num_symbols);
+  T.catch_all = groups->catch_all;
+  T.start_state = dfa->start_state;
+  T.invalid_state = dfa->invalid_state;
+  T.accept_mask = dfa->accept_mask;
+  T.num_columns = static_cast<uint8_t>(schema->num_columns);
+  uint32_t ns = 0, nn = 0;
+  for (uint32_t c = 0; c < schema->num_columns; ++c) {
+    const uint32_t ty = schema->types[c];
+    if (ty > PP_TIMESTAMP_CLF) { delete P; return PP_E_BAD_TABLE; }
+    P->types[c] = ty;
+    T.col_type[c] = static_cast<uint8_t>(ty);
+    T.str_slot[c] = 0xFF;
+    T.num_slot[c] = 0xFF;
+    if (ty == PP_STRING) {
+      if (ns >= PP_MAX_STRING_COLUMNS) { delete P; return PP_E_UNSUPPORTED; }
+      T.str_slot[c] = static_cast<uint8_t>(ns++);
+    } else {
+      T.num_slot[c] = static_cast<uint8_t>(nn++);
+    }
+  }
+  T.num_str = static_cast<uint8_t>(ns);
+  T.num_num = static_cast<uint8_t>(nn);
+  *out = P;
+  return PP_OK;
+}
+
+extern "C" void parparaw_destroy(pp_parser* parser) { delete parser; }
+
+extern "C" pp_status parparaw_set_option(pp_parser* P, pp_option option, int64_t value) {
+  if (P == nullptr) return PP_E_ARG;
+  switch (option) {
+    case PP_OPT_TILE_CONFIG:
+      if (value < 0 || value > 4) return PP_E_ARG;
+      P->tile_config = static_cast<int>(value);
+      return PP_OK;
+    case PP_OPT_TIMEOUT_MS:
+      if (value <= 0) return PP_E_ARG;
+      P->timeout_ns = static_cast<uint64_t>(value) * 1000000ull;
+      return PP_OK;
+    case PP_OPT_GRID_LIMIT:
+      if (value < 0) return PP_E_ARG;
+      P->grid_limit = value;
+      return PP_OK;
+    default:
+      return PP_E_ARG;
+  }
+}
+
+extern "C" pp_status parparaw_get_info(const pp_parser* P, pp_parser_info* info) {
+  if (P == nullptr || info == nullptr) return PP_E_ARG;
+  const ShapeInfo sh = shape_for(P->tile_config);
+  info->num_states = P->tab.num_states;
+  info->num_groups = P->tab.num_groups;
+  info->num_symbols = P->tab.num_symbols;
+  info->num_columns = P->tab.num_columns;
+  info->num_string_columns = P->tab.num_str;
+  info->catch_all_idempotent = P->tab.idempotent;
+  info->tile_bytes = static_cast<uint32_t>(sh.tile_bytes);
+  info->threads_per_block = static_cast<uint32_t>(sh.threads);
+  return PP_OK;
+}
+
+extern "C" pp_status parparaw_set_kernel_events(pp_parser* P, void* start_event, void* stop_event) {
+  if (P == nullptr || ((start_event == nullptr) != (stop_event == nullptr))) return PP_E_ARG;
+  P->ev_start = static_cast<cudaEvent_t>(start_event);
+  P->ev_stop = static_cast<cudaEvent_t>(stop_event);
+  return PP_OK;
+}
+
+extern "C" pp_status parparaw_parse(const pp_parser* P, const uint8_t* input, uint64_t len,
+                                    const pp_columns* out, void* stream_) {
+  if (P == nullptr || (input == nullptr && len > 0)) return PP_E_ARG;
+  pp_status st = check_columns(P, out);
+  if (st != PP_OK) return st;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const ShapeInfo shape = shape_for(P->tile_config);
+
+  Launch* Lp = new (std::nothrow) Launch();
+  if (Lp == nullptr) return PP_E_NOMEM;
+  Launch& L = *Lp;
+  std::memset(&L, 0, sizeof(L));
+  Job& J = L.job0;
+  J.input = input;
+  J.len = len;
+  J.head = len > 0 ? (reinterpret_cast<uintptr_t>(input) & 15u) : 0;
+  J.ntiles = len > 0 ? (J.head + len + shape.tile_bytes - 1) / shape.tile_bytes : 0;
+  J.tile_base = 0;
+  J.rows_cap = out->rows_cap;
+  J.bit_words = (out->rows_cap + 31) / 32 + 1;
+  J.row_valid = out->row_valid;
+  J.result = out->result;
+  L.tables0 = P->tab;
+  for (uint32_t c = 0; c < out->num_columns; ++c) {
+    L.cols0[c].values = out->cols[c].values;
+    L.cols0[c].offsets = out->cols[c].offsets;
+    L.cols0[c].validity = out->cols[c].validity;
+    L.cols0[c].values_cap = out->cols[c].values_cap;
+  }
+  const ScratchPlan plan = plan_scratch(64, J.ntiles, P->tab.num_str, P->tab.num_num, J.bit_words);
+  uint8_t* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), plan.total, stream);
+  if (e != cudaSuccess) {
+    delete Lp;
+    return map_err(e);
+  }
+  fill_job(J, plan, scratch);
+  L.jobs = nullptr;
+  L.cols = nullptr;
+  L.tables = nullptr;
+  L.njobs = 1;
+  L.total_tiles = J.ntiles;
+  L.work_counter = reinterpret_cast<unsigned long long*>(scratch);
+  L.timeout_ns = P->timeout_ns;
+  st = run_launch(L, shape, nspec_of(P->tab), P->grid_limit, P, stream, 1, J.ntiles, J.bit_words);
+  cudaFreeAsync(scratch, stream);
+  delete Lp;
+  return st;
+}
+
+extern "C" pp_status parparaw_parse_batch(const pp_batch_item* items, uint64_t n, void* stream_) {
+  if (items == nullptr && n > 0) return PP_E_ARG;
+  if (n == 0) return PP_OK;
+  if (n > 0xFFFFFFFFull) return PP_E_UNSUPPORTED;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const pp_parser* first = items[0].parser;
+  if (first == nullptr) return PP_E_ARG;
+  const ShapeInfo shape = shape_for(first->tile_config);
+
+  std::vector<Tables> tables;
+  std::unordered_map<const pp_parser*, uint32_t> table_index;
+  std::vector<Job> jobs(n);
+  std::vector<Col> cols;
+  std::vector<ScratchPlan> plans(n);
+  int nspec = 4;
+  uint64_t total_tiles = 0, max_tiles = 0, max_words = 0;
+  size_t scratch_bytes = 64;
+  for (uint64_t i = 0; i < n; ++i) {
+    const pp_batch_item& it = items[i];
+    if (it.parser == nullptr || (it.input == nullptr && it.len > 0)) return PP_E_ARG;
+    pp_status st = check_columns(it.parser, it.out);
+    if (st != PP_OK) return st;
+    auto found = table_index.find(it.parser);
+    uint32_t ti;
+    if (found == table_index.end()) {
+      ti = static_cast<uint32_t>(tables.size());
+      tables.push_back(it.parser->tab);
+      table_index[it.parser] = ti;
+      nspec = std::max(nspec, nspec_of(it.parser->tab));
+    } else {
+      ti = found->second;
+    }
+    Job& J = jobs[i];
+    std::memset(&J, 0, sizeof(J));
+    J.input = it.input;
+    J.len = it.len;
+    J.head = it.len > 0 ? (reinterpret_cast<uintptr_t>(it.input) & 15u) : 0;
+    J.ntiles = it.len > 0 ? (J.head + it.len + shape.tile_bytes - 1) / shape.tile_bytes : 0;
+    J.tile_base = total_tiles;
+    J.rows_cap = it.out->rows_cap;
+    J.bit_words = (it.out->rows_cap + 31) / 32 + 1;
+    J.row_valid = it.out->row_valid;
+    J.result = it.out->result;
+    J.tables = ti;
+    J.col0 = static_cast<uint32_t>(cols.size());
+    for (uint32_t c = 0; c < it.out->num_columns; ++c) {
+      Col col;
+      col.values = it.out->cols[c].values;
+      col.offsets = it.out->cols[c].offsets;
+      col.validity = it.out->cols[c].validity;
+      col.values_cap = it.out->cols[c].values_cap;
+      cols.push_back(col);
+    }
+    plans[i] = plan_scratch(scratch_bytes, J.ntiles, it.parser->tab.num_str, it.parser->tab.num_num,
+                            J.bit_words);
+    scratch_bytes = plans[i].total;
+    total_tiles += J.ntiles;
+    max_tiles = std::max(max_tiles, J.ntiles);
+    max_words = std::max(max_words, J.bit_words);
+  }
+  const size_t off_tables = align_up(scratch_bytes, 256);
+  const size_t off_jobs = align_up(off_tables + sizeof(Tables) * tables.size(), 256);
+  const size_t off_cols = align_up(off_jobs + sizeof(Job) * jobs.size(), 256);
+  const size_t total = align_up(off_cols + sizeof(Col) * cols.size(), 256);
+  uint8_t* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), total, stream);
+  if (e != cudaSuccess) return map_err(e);
+  for (uint64_t i = 0; i < n; ++i) fill_job(jobs[i], plans[i], scratch);
+  // one host staging buffer, copied in one transfer
+  std::vector<uint8_t> host(total - off_tables);
+  std::memcpy(host.data(), tables.data(), sizeof(Tables) * tables.size());
+  std::memcpy(host.data() + (off_jobs - off_tables), jobs.data(), sizeof(Job) * jobs.size());
+  std::memcpy(host.data() + (off_cols - off_tables), cols.data(), sizeof(Col) * cols.size());
+  e = cudaMemcpyAsync(scratch + off_tables, host.data(), host.size(), cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(scratch, stream);
+    return map_err(e);
+  }
+  Launch* Lp = new (std::nothrow) Launch();
+  if (Lp == nullptr) {
+    cudaFreeAsync(scratch, stream);
+    return PP_E_NOMEM;
+  }
+  Launch& L = *Lp;
+  std::memset(&L, 0, sizeof(L));
+  L.tables = reinterpret_cast<const Tables*>(scratch + off_tables);
+  L.jobs = reinterpret_cast<const Job*>(scratch + off_jobs);
+  L.cols = reinterpret_cast<const Col*>(scratch + off_cols);
+  L.njobs = static_cast<uint32_t>(n);
+  L.total_tiles = total_tiles;
+  L.work_counter = reinterpret_cast<unsigned long long*>(scratch);
+  L.timeout_ns = first->timeout_ns;
+  pp_status st = run_launch(L, shape, nspec, first->grid_limit, first, stream,
+                            static_cast<uint32_t>(std::min<uint64_t>(n, 65535)), max_tiles, max_words);
+  cudaFreeAsync(scratch, stream);
+  delete Lp;
+  return st;
+}

@@ -1,0 +1,775 @@
+// pp_kernel.cuh -- the single-pass ParPaRaw tile kernel for sm_103a.
+//
+// One block owns one tile of T = NT * B input bytes at a time (B = 16 * VPT
+// bytes per thread, the paper's per-thread chunk, Sec. 3) and takes tiles
+// from a device work counter, so a tile's predecessors always belong to
+// blocks that are already running.  Per tile:
+//
+//   load    TMA bulk copy of the tile into shared memory (ragged ends by
+//           plain loads); 16-byte vector reads per thread.
+//   a1, a2  symbol matching (SWAR zero-byte tests against the symbols,
+//           Sec. 4.5) and multi-state simulation of the chunk: one DFA
+//           instance per state, packed as a state-transition vector
+//           (Sec. 3.1).  Runs of catch-all symbols collapse into one
+//           transition when the catch-all transition is idempotent.
+//   a3      exclusive o-scan of the vectors: block scan, then decoupled
+//           look-back over the tiles' status words (chain 1).
+//   a4      re-simulation from the chunk's start state emitting the data /
+//           field / record / control tags as bit masks (Sec. 3.1).
+//   a5      record counts (popcount) and absolute/relative column offsets
+//           (Sec. 3.2): block scan + look-back (chain 2).  Then the bytes
+//           every string column receives: block scan + look-back (chain 3).
+//   a6      stable partition: each string field's data bytes are gathered
+//           in shared memory in column order and written with TMA bulk
+//           stores; Arrow int64 offsets are written at field ends (Sec. 3.3).
+//   a7      numeric fields are converted by the thread holding the
+//           delimiter that opens them (Sec. 3.3).
+//   a8      invalid transitions, field-count mismatches and conversion
+//           failures are recorded; the finalize kernel turns them into
+//           validity bitmaps and the result.
+//
+// Every spin (mbarrier, look-back) is bounded by %globaltimer and reports
+// PP_E_TIMEOUT instead of hanging.
+#pragma once
+#include <cstdint>
+
+#include "pp_convert.cuh"
+#include "pp_device.cuh"
+#include "pp_types.h"
+
+namespace pp {
+
+template <int NT_, int VPT_>
+struct TileShape {
+  static constexpr int NT = NT_;
+  static constexpr int VPT = VPT_;
+  static constexpr int B = 16 * VPT;       // bytes per thread (chunk)
+  static constexpr int T = NT * B;         // bytes per tile
+  static constexpr int MW = (B + 63) / 64; // 64-bit mask words per chunk
+  static constexpr int NW = NT / 32;
+  static constexpr int kStage = T + 32 * PP_MAX_STRING_COLUMNS + 64;
+};
+
+struct SmemHead {
+  uint64_t mbar;
+  unsigned long long item;
+  uint32_t job;
+  int32_t tables_loaded;
+  uint64_t prefix_vec;   // chain 1 exclusive prefix of this tile
+  uint64_t prefix_rc;    // chain 2 exclusive prefix of this tile
+  int64_t col_base[PP_MAX_STRING_COLUMNS];   // chain 3 exclusive prefix
+  uint32_t tile_tot[PP_MAX_STRING_COLUMNS];
+  uint32_t stage_off[PP_MAX_STRING_COLUMNS];
+  uint64_t wsum64[32];
+  uint32_t wsum32[32];
+  uint32_t wsumk[PP_MAX_STRING_COLUMNS / 2][32];
+  Tables tab;
+  uint8_t str_col[PP_MAX_STRING_COLUMNS];  // slot -> column
+};
+
+template <class Shape>
+struct SmemLayout {
+  static constexpr size_t kHead = (sizeof(SmemHead) + 127) & ~size_t(127);
+  static constexpr size_t kTile = kHead;
+  static constexpr size_t kStage = kTile + ((Shape::T + 64 + 127) & ~size_t(127));
+  static constexpr size_t kDm = kStage + ((Shape::kStage + 127) & ~size_t(127));
+  static constexpr size_t kDl = kDm + sizeof(uint64_t) * Shape::NT * Shape::MW;
+  static constexpr size_t kCnt = kDl + sizeof(uint64_t) * Shape::NT * Shape::MW;
+  static constexpr size_t kBytes = kCnt + sizeof(uint16_t) * Shape::NT * PP_MAX_STRING_COLUMNS;
+};
+
+// ---------------------------------------------------- look-back (1 word) ---
+
+struct StatePolicy {  // chain 1: state-transition vectors, composite operator
+  static __device__ __forceinline__ uint64_t to_word(uint64_t v) { return vpack(v); }
+  static __device__ __forceinline__ uint64_t from_word(uint64_t w) {
+    return vunpack(static_cast<uint32_t>(w));
+  }
+  static __device__ __forceinline__ uint64_t combine(uint64_t a, uint64_t b) { return vcompose(a, b); }
+  static constexpr uint64_t kIdentity = kIdentityVec;
+};
+struct RcPolicy {  // chain 2: records and column offsets
+  static __device__ __forceinline__ uint64_t to_word(uint64_t v) { return v; }
+  static __device__ __forceinline__ uint64_t from_word(uint64_t w) { return w & ~kFlagMask; }
+  static __device__ __forceinline__ uint64_t combine(uint64_t a, uint64_t b) { return tc_combine(a, b); }
+  static constexpr uint64_t kIdentity = 0;
+};
+
+// Called by one full warp.  Publishes the tile's aggregate, walks back over
+// predecessors (32 at a time) until an inclusive prefix is found, publishes
+// the tile's inclusive prefix and returns the exclusive one.  `first` is the
+// prefix of tile 0.
+template <class P>
+__device__ uint64_t lookback_word(uint64_t* st, uint64_t t, uint64_t agg, uint64_t first,
+                                  uint64_t deadline, Misc* misc) {
+  const int lane = threadIdx.x & 31;
+  if (t == 0) {
+    if (lane == 0) st_release_u64(&st[0], kFlagInc | P::to_word(P::combine(first, agg)));
+    return first;
+  }
+  if (lane == 0) st_release_u64(&st[t], kFlagAgg | P::to_word(agg));
+  uint64_t acc = P::kIdentity;
+  int64_t idx = static_cast<int64_t>(t) - 1;
+  for (;;) {
+    const int64_t mine = idx - lane;
+    uint64_t w = kFlagInc | P::to_word(P::kIdentity);
+    if (mine >= 0) {
+      w = ld_acquire_u64(&st[mine]);
+      while ((w & kFlagMask) == 0) {
+        if (globaltimer_ns() > deadline) {
+          atomicOr(&misc->timeout, 1u);
+          w = kFlagInc | P::to_word(P::kIdentity);
+          break;
+        }
+        __nanosleep(32);
+        w = ld_acquire_u64(&st[mine]);
+      }
+    }
+    const uint32_t incmask = __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagInc);
+    const int firstinc = incmask ? __ffs(incmask) - 1 : 32;
+    uint64_t v = lane <= firstinc ? P::from_word(w) : P::kIdentity;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint64_t o = __shfl_down_sync(0xffffffffu, v, off);
+      if (lane + off < 32) v = P::combine(o, v);  // o holds earlier tiles
+    }
+    v = __shfl_sync(0xffffffffu, v, 0);
+    acc = P::combine(v, acc);
+    if (incmask) break;
+    idx -= 32;
+  }
+  if (lane == 0) st_release_u64(&st[t], kFlagInc | P::to_word(P::combine(acc, agg)));
+  return acc;
+}
+
+// ------------------------------------------------------ mask helpers ---
+
+template <int MW>
+__device__ __forceinline__ void set_range(uint64_t (&m)[MW], int lo, int hi) {
+#pragma unroll
+  for (int w = 0; w < MW; ++w) m[w] |= bit_range(lo - 64 * w, hi - 64 * w);
+}
+template <int MW>
+__device__ __forceinline__ int popc_range(const uint64_t (&m)[MW], int lo, int hi) {
+  int n = 0;
+#pragma unroll
+  for (int w = 0; w < MW; ++w) n += __popcll(m[w] & bit_range(lo - 64 * w, hi - 64 * w));
+  return n;
+}
+// first position >= x (and < end) whose bit equals `one`, else end
+template <int MW>
+__device__ __forceinline__ int next_bit(const uint64_t (&m)[MW], int x, int end, bool one) {
+#pragma unroll
+  for (int w = 0; w < MW; ++w) {
+    const uint64_t v = (one ? m[w] : ~m[w]) & ~bits_below(x - 64 * w);
+    if (v && 64 * w + 63 >= x) return min(64 * w + __ffsll(static_cast<long long>(v)) - 1, end);
+  }
+  return end;
+}
+template <int MW>
+__device__ __forceinline__ bool test_bit(const uint64_t (&m)[MW], int p) {
+  bool r = false;
+#pragma unroll
+  for (int w = 0; w < MW; ++w)
+    if ((p >> 6) == w) r = (m[w] >> (p & 63)) & 1ull;
+  return r;
+}
+
+// shared -> shared byte copy with 32-bit stores where the destination allows
+__device__ __forceinline__ void smem_copy(uint8_t* dst, const uint8_t* src, int n) {
+  while (n > 0 && (reinterpret_cast<uintptr_t>(dst) & 3)) {
+    *dst++ = *src++;
+    --n;
+  }
+  const int nw = n >> 2;
+  if (nw > 0) {
+    const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 3) * 8;
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(reinterpret_cast<uintptr_t>(src) & ~uintptr_t(3));
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    if (sh == 0) {
+      for (int k = 0; k < nw; ++k) d[k] = s[k];
+    } else {
+      uint32_t lo = s[0];
+      for (int k = 0; k < nw; ++k) {
+        const uint32_t hi = s[k + 1];
+        d[k] = __funnelshift_r(lo, hi, sh);
+        lo = hi;
+      }
+    }
+    dst += 4 * nw;
+    src += 4 * nw;
+    n -= 4 * nw;
+  }
+  while (n-- > 0) *dst++ = *src++;
+}
+
+__device__ __forceinline__ void store_value(const Col& col, uint32_t type, uint64_t r, uint64_t v) {
+  if (type == PP_INT32 || type == PP_DATE_D)
+    static_cast<uint32_t*>(col.values)[r] = static_cast<uint32_t>(v);
+  else
+    static_cast<uint64_t*>(col.values)[r] = v;
+}
+
+// ------------------------------------------------------------- kernel ---
+
+template <class Shape, int NSPEC>
+__global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constant__ Launch L) {
+  constexpr int NT = Shape::NT, VPT = Shape::VPT, B = Shape::B, T = Shape::T, MW = Shape::MW;
+  using Lay = SmemLayout<Shape>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  SmemHead* H = reinterpret_cast<SmemHead*>(smem);
+  uint8_t* s_tile = smem + Lay::kTile;
+  uint8_t* s_stage = smem + Lay::kStage;
+  uint64_t* s_dm = reinterpret_cast<uint64_t*>(smem + Lay::kDm);
+  uint64_t* s_dl = reinterpret_cast<uint64_t*>(smem + Lay::kDl);
+  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + Lay::kCnt);
+  const Tables& TB = H->tab;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&H->mbar, 1);
+    fence_mbar_init();
+    H->tables_loaded = -1;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  bool pending_store = false;
+
+  for (;;) {
+    // ------------------------------------------------------------ work item
+    if (tid == 0) {
+      if (pending_store) bulk_wait_read_all();  // staging is reused below
+      const unsigned long long item = atomicAdd(L.work_counter, 1ull);
+      uint32_t j = 0;
+      if (L.jobs != nullptr && item < L.total_tiles) {
+        uint32_t lo = 0, hi = L.njobs - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (L.jobs[mid].tile_base <= item) lo = mid; else hi = mid - 1;
+        }
+        j = lo;
+      }
+      H->item = item;
+      H->job = j;
+    }
+    pending_store = false;
+    __syncthreads();
+    const unsigned long long item = H->item;
+    if (item >= L.total_tiles) break;
+    const Job& J = L.jobs ? L.jobs[H->job] : L.job0;
+    const Col* cols = L.jobs ? (L.cols + J.col0) : L.cols0;
+    const uint64_t deadline = globaltimer_ns() + L.timeout_ns;
+
+    if (H->tables_loaded != static_cast<int32_t>(J.tables)) {
+      const Tables* src = L.jobs ? &L.tables[J.tables] : &L.tables0;
+      __syncthreads();
+      const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+      uint32_t* d32 = reinterpret_cast<uint32_t*>(&H->tab);
+      for (int i = tid; i < static_cast<int>(sizeof(Tables) / 4); i += NT) d32[i] = s32[i];
+      __syncthreads();
+      if (tid < PP_MAX_STRING_COLUMNS) {
+        uint8_t col = 0xFF;
+        for (int c = 0; c < H->tab.num_columns; ++c)
+          if (H->tab.str_slot[c] == tid) col = static_cast<uint8_t>(c);
+        H->str_col[tid] = col;
+      }
+      if (tid == 0) H->tables_loaded = static_cast<int32_t>(J.tables);
+      __syncthreads();
+    }
+
+    // ------------------------------------------------------- load the tile
+    const uint64_t t = item - J.tile_base;
+    const uint64_t VL = J.head + J.len;  // virtual length (16-byte aligned origin)
+    const uint64_t v0 = t * T;
+    const uint64_t v1 = min(v0 + T, VL);
+    const uint8_t* vbase = J.input - J.head;
+    const uint64_t a16 = max(v0, (J.head + 15) & ~uint64_t(15));
+    const uint64_t b16 = min(v1, VL & ~uint64_t(15));
+    const uint32_t bulk = b16 > a16 ? static_cast<uint32_t>(b16 - a16) : 0u;
+    if (tid == 0 && bulk > 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&H->mbar, bulk);
+      tma_load_1d(s_tile + (a16 - v0), vbase + a16, bulk, &H->mbar);
+    }
+    {
+      const uint64_t lo_v = max(v0, J.head);
+      if (bulk == 0) {
+        for (uint64_t x = lo_v + tid; x < v1; x += NT) s_tile[x - v0] = vbase[x];
+      } else if (tid < 32) {
+        const uint64_t x = tid < 16 ? lo_v + tid : b16 + (tid - 16);
+        const bool in_head = tid < 16 && x < a16 && x < v1;
+        const bool in_tail = tid >= 16 && x < v1;
+        if (in_head || in_tail) s_tile[x - v0] = vbase[x];
+      }
+    }
+    if (bulk > 0) {
+      while (!mbar_try_wait(&H->mbar, phase)) {
+        if (globaltimer_ns() > deadline + 1000000000ull) {
+          if (tid == 0) atomicOr(&J.misc->timeout, 1u);
+          break;
+        }
+      }
+      phase ^= 1u;
+    }
+    __syncthreads();
+
+    // valid bytes of this thread's chunk, chunk-relative [lo, hi)
+    const int64_t cv0 = static_cast<int64_t>(v0) + static_cast<int64_t>(tid) * B;
+    int lo = static_cast<int>(min(max(static_cast<int64_t>(J.head) - cv0, int64_t(0)), int64_t(B)));
+    int hi = static_cast<int>(min(max(static_cast<int64_t>(VL) - cv0, int64_t(0)), int64_t(B)));
+    if (hi < lo) hi = lo;
+    const uint8_t* chunk = s_tile + tid * B;
+
+    // --------------------------------------------- a1: symbol matching
+    uint64_t spec[MW];
+#pragma unroll
+    for (int w = 0; w < MW; ++w) spec[w] = 0;
+    if (!TB.idempotent) {
+      set_range(spec, lo, hi);  // every symbol is simulated on its own
+    } else if (TB.num_symbols > 0) {
+      uint32_t rep[NSPEC];
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) rep[s] = TB.rep[s < TB.num_symbols ? s : 0];
+      const uint4* src = reinterpret_cast<const uint4*>(chunk);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const uint4 q = src[v];
+        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          uint32_t acc = 0;
+#pragma unroll
+          for (int s = 0; s < NSPEC; ++s) {
+            const uint32_t x = wd[k] ^ rep[s];
+            acc |= (x - 0x01010101u) & ~x;  // some byte of x is zero
+          }
+          if (acc & 0x80808080u) {
+            uint32_t m = 0;
+#pragma unroll
+            for (int s = 0; s < NSPEC; ++s) {
+              const uint32_t x = wd[k] ^ rep[s];
+              m |= ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x);  // exactly the zero bytes
+            }
+            m &= 0x80808080u;
+            const uint32_t bits4 = (((m >> 7) * 0x00204081u) >> 21) & 0xFu;
+            const int pos = 16 * v + 4 * k;
+            spec[pos >> 6] |= static_cast<uint64_t>(bits4) << (pos & 63);
+          }
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < MW; ++w) spec[w] &= bit_range(lo - 64 * w, hi - 64 * w);
+    }
+
+    // ------------------------------------ a2: multi-state simulation
+    uint64_t vec = kIdentityVec;
+    {
+      int prev = -1;
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {
+        uint64_t m = spec[w];
+        while (m) {
+          const int p = 64 * w + __ffsll(static_cast<long long>(m)) - 1;
+          m &= m - 1;
+          const bool run = max(prev + 1, lo) < p;
+          const uint32_t g = TB.group_of[chunk[p]];
+          vec = vcompose(vec, run ? TB.trans_run[g] : TB.trans[g]);
+          prev = p;
+        }
+      }
+      if (max(prev + 1, lo) < hi) vec = vcompose(vec, TB.trans[TB.catch_all]);
+    }
+
+    // ------------------------------------------- a3: o-scan + chain 1
+    uint64_t tile_vec;
+    const uint64_t vex = block_exclusive_scan<NT>(
+        vec, [](uint64_t a, uint64_t b) { return vcompose(a, b); }, kIdentityVec, H->wsum64,
+        &tile_vec);
+    if (warp == 0) {
+      const uint64_t pre =
+          lookback_word<StatePolicy>(J.st_state, t, tile_vec, kIdentityVec, deadline, J.misc);
+      if (lane == 0) H->prefix_vec = pre;
+    }
+    __syncthreads();
+    const uint32_t tile_s0 = vget(H->prefix_vec, TB.start_state);
+    const uint32_t tile_send = vget(tile_vec, tile_s0);
+    const uint32_t s_start = vget(vex, tile_s0);
+
+    // ------------------------------------------- a4: re-simulation, tags
+    uint64_t dm[MW], fm[MW], rm[MW];
+#pragma unroll
+    for (int w = 0; w < MW; ++w) dm[w] = fm[w] = rm[w] = 0;
+    uint32_t s_end;
+    {
+      const uint32_t inv = TB.invalid_state;
+      const uint32_t ca = TB.catch_all;
+      const uint32_t e_ca = TB.emit[ca];
+      const uint64_t t_ca = TB.trans[ca];
+      uint32_t s = s_start;
+      int prev = -1, inv_pos = -1;
+      auto run = [&](int rs, int re) {
+        const uint32_t s1 = vget(t_ca, s);
+        const uint32_t tag0 = (e_ca >> (2 * s)) & 3u, tagr = (e_ca >> (2 * s1)) & 3u;
+        if (s != inv && s1 == inv && inv_pos < 0) inv_pos = rs;
+#pragma unroll
+        for (int w = 0; w < MW; ++w) {
+          const uint64_t b0 = bit_range(rs - 64 * w, rs + 1 - 64 * w);
+          const uint64_t br = bit_range(rs + 1 - 64 * w, re - 64 * w);
+          dm[w] |= (tag0 == PP_TAG_DATA ? b0 : 0) | (tagr == PP_TAG_DATA ? br : 0);
+          fm[w] |= (tag0 == PP_TAG_FIELD ? b0 : 0) | (tagr == PP_TAG_FIELD ? br : 0);
+          rm[w] |= (tag0 == PP_TAG_RECORD ? b0 : 0) | (tagr == PP_TAG_RECORD ? br : 0);
+        }
+        s = s1;
+      };
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {
+        uint64_t m = spec[w];
+        while (m) {
+          const int p = 64 * w + __ffsll(static_cast<long long>(m)) - 1;
+          m &= m - 1;
+          const int rs = max(prev + 1, lo);
+          if (rs < p) run(rs, p);
+          const uint32_t g = TB.group_of[chunk[p]];
+          const uint32_t tag = (TB.emit[g] >> (2 * s)) & 3u;
+          const uint32_t ns = vget(TB.trans[g], s);
+          if (s != inv && ns == inv && inv_pos < 0) inv_pos = p;
+          const uint64_t bit = 1ull << (p & 63);
+          if (tag == PP_TAG_DATA) dm[w] |= bit;
+          else if (tag == PP_TAG_FIELD) fm[w] |= bit;
+          else if (tag == PP_TAG_RECORD) rm[w] |= bit;
+          s = ns;
+          prev = p;
+        }
+      }
+      {
+        const int rs = max(prev + 1, lo);
+        if (rs < hi) run(rs, hi);
+      }
+      s_end = s;
+      if (inv_pos >= 0)
+        atomicMin(&J.misc->first_invalid,
+                  static_cast<unsigned long long>(cv0 + inv_pos - static_cast<int64_t>(J.head)));
+    }
+#pragma unroll
+    for (int w = 0; w < MW; ++w) {
+      s_dm[tid * MW + w] = dm[w];
+      s_dl[tid * MW + w] = fm[w] | rm[w];
+    }
+
+    // ---------------------------------- a5: records, columns + chain 2
+    uint32_t nrec = 0, ncol = 0;
+    {
+      int last_rd = -1;
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {
+        nrec += __popcll(rm[w]);
+        if (rm[w]) last_rd = 64 * w + 63 - __clzll(static_cast<long long>(rm[w]));
+      }
+#pragma unroll
+      for (int w = 0; w < MW; ++w) ncol += __popcll(fm[w] & ~bits_below(last_rd + 1 - 64 * w));
+    }
+    uint32_t rc_tile;
+    const uint32_t rc_ex = block_exclusive_scan<NT>(rc_pack(nrec, ncol, nrec > 0), rc_combine,
+                                                    rc_pack(0, 0, false), H->wsum32, &rc_tile);
+    if (warp == 0) {
+      const uint64_t agg = tc_pack(rc_tile & 0xFFFFu, (rc_tile >> 16) & kColSat, (rc_tile >> 31) != 0);
+      const uint64_t pre = lookback_word<RcPolicy>(J.st_rc, t, agg, tc_pack(0, 0, true), deadline, J.misc);
+      if (lane == 0) H->prefix_rc = pre;
+    }
+    __syncthreads();
+    const uint64_t tile_row0 = H->prefix_rc & kRecMask;
+    const uint32_t tile_col0 = static_cast<uint32_t>((H->prefix_rc >> 40) & 0x1FFFFF);
+    const uint64_t row_start = tile_row0 + (rc_ex & 0xFFFFu);
+    const uint32_t col_start = (rc_ex >> 31) ? ((rc_ex >> 16) & kColSat)
+                                             : min(tile_col0 + ((rc_ex >> 16) & kColSat), kColSat);
+
+    const uint32_t C = TB.num_columns;
+    const uint32_t NS = TB.num_str;
+    // ------------------------------- string bytes per column + chain 3
+    if (NS > 0) {
+      for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
+      uint32_t c = col_start;
+      int pos = lo;
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {
+        uint64_t dl = fm[w] | rm[w];
+        while (dl) {
+          const int d = 64 * w + __ffsll(static_cast<long long>(dl)) - 1;
+          dl &= dl - 1;
+          if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += popc_range(dm, pos, d);
+          c = ((rm[w] >> (d & 63)) & 1ull) ? 0u : min(c + 1, kColSat);
+          pos = d + 1;
+        }
+      }
+      if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += popc_range(dm, pos, hi);
+
+      // block scan of the per-slot counts, two 16-bit slots per word
+      const uint32_t K = (NS + 1) / 2;
+      uint32_t incl[PP_MAX_STRING_COLUMNS / 2], own[PP_MAX_STRING_COLUMNS / 2];
+#pragma unroll
+      for (int k = 0; k < PP_MAX_STRING_COLUMNS / 2; ++k) {
+        if (k < static_cast<int>(K)) {
+          own[k] = s_cnt[(2 * k) * NT + tid] |
+                   (2 * k + 1 < static_cast<int>(NS) ? (static_cast<uint32_t>(s_cnt[(2 * k + 1) * NT + tid]) << 16) : 0u);
+          incl[k] = warp_inclusive_scan(own[k], [](uint32_t a, uint32_t b) { return a + b; }, lane);
+          if (lane == 31) H->wsumk[k][warp] = incl[k];
+        }
+      }
+      __syncthreads();
+      if (warp == 0) {
+        for (uint32_t k = 0; k < K; ++k) {
+          uint32_t x = lane < Shape::NW ? H->wsumk[k][lane] : 0u;
+          x = warp_inclusive_scan(x, [](uint32_t a, uint32_t b) { return a + b; }, lane);
+          if (lane < Shape::NW) H->wsumk[k][lane] = x;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < PP_MAX_STRING_COLUMNS / 2; ++k) {
+        if (k < static_cast<int>(K)) {
+          const uint32_t ex = incl[k] - own[k] + (warp > 0 ? H->wsumk[k][warp - 1] : 0u);
+          s_cnt[(2 * k) * NT + tid] = static_cast<uint16_t>(ex & 0xFFFFu);
+          if (2 * k + 1 < static_cast<int>(NS)) s_cnt[(2 * k + 1) * NT + tid] = static_cast<uint16_t>(ex >> 16);
+          if (tid == 0) {
+            const uint32_t tot = H->wsumk[k][Shape::NW - 1];
+            H->tile_tot[2 * k] = tot & 0xFFFFu;
+            if (2 * k + 1 < static_cast<int>(NS)) H->tile_tot[2 * k + 1] = tot >> 16;
+          }
+        }
+      }
+      __syncthreads();
+
+      // chain 3: per-slot byte counts, summed over the predecessors
+      if (warp == 0) {
+        int64_t* agg = J.st_bytes_agg + t * NS;
+        int64_t* inc = J.st_bytes_inc + t * NS;
+        int64_t acc[PP_MAX_STRING_COLUMNS];
+#pragma unroll
+        for (int k = 0; k < PP_MAX_STRING_COLUMNS; ++k) acc[k] = 0;
+        if (t > 0) {
+          if (lane < static_cast<int>(NS)) st_relaxed_s64(&agg[lane], H->tile_tot[lane]);
+          __syncwarp();
+          __threadfence();
+          if (lane == 0) st_release_u32(&J.st_bytes_flag[t], 1u);
+          int64_t idx = static_cast<int64_t>(t) - 1;
+          for (;;) {
+            const int64_t mine = idx - lane;
+            uint32_t f = 2u;
+            if (mine >= 0) {
+              f = ld_acquire_u32(&J.st_bytes_flag[mine]);
+              while (f == 0u) {
+                if (globaltimer_ns() > deadline) {
+                  atomicOr(&J.misc->timeout, 1u);
+                  f = 3u;
+                  break;
+                }
+                __nanosleep(32);
+                f = ld_acquire_u32(&J.st_bytes_flag[mine]);
+              }
+            }
+            const uint32_t incmask = __ballot_sync(0xffffffffu, f >= 2u);
+            const int firstinc = incmask ? __ffs(incmask) - 1 : 32;
+            const bool use = mine >= 0 && lane <= firstinc && f != 3u;
+            const int64_t* src = (f == 2u ? J.st_bytes_inc : J.st_bytes_agg) + (mine >= 0 ? mine : 0) * NS;
+#pragma unroll
+            for (int k = 0; k < PP_MAX_STRING_COLUMNS; ++k) {
+              if (k < static_cast<int>(NS)) {
+                long long x = use ? ld_relaxed_s64(&src[k]) : 0ll;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+                acc[k] += x;
+              }
+            }
+            if (incmask) break;
+            idx -= 32;
+          }
+        }
+        if (lane < static_cast<int>(NS)) {
+          int64_t mine_acc = 0;
+#pragma unroll
+          for (int k = 0; k < PP_MAX_STRING_COLUMNS; ++k)
+            if (k == lane) mine_acc = acc[k];
+          H->col_base[lane] = mine_acc;
+          st_relaxed_s64(&inc[lane], mine_acc + H->tile_tot[lane]);
+        }
+        __syncwarp();
+        __threadfence();
+        if (lane == 0) st_release_u32(&J.st_bytes_flag[t], 2u);
+        if (lane == 0) {
+          // staging regions share the destination's 16-byte phase so that
+          // their aligned interiors can be bulk-stored
+          uint32_t off = 0;
+          for (uint32_t k = 0; k < NS; ++k) {
+            const uint8_t* dst = static_cast<const uint8_t*>(cols[H->str_col[k]].values) + H->col_base[k];
+            off = ((off + 15u) & ~15u) + static_cast<uint32_t>(reinterpret_cast<uintptr_t>(dst) & 15u);
+            H->stage_off[k] = off;
+            off += H->tile_tot[k];
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    // ----------------- a6 / a7 / a8: gather, offsets, conversion, rejects
+    const bool last_tile = (t + 1 == J.ntiles);
+    const uint64_t rows_cap = J.rows_cap;
+    auto record_end = [&](uint64_t r, uint32_t nfields) {
+      if (r >= rows_cap) return;
+      if (nfields != C) atomicOr(&J.fail_bits[r >> 5], 1u << (r & 31));
+      for (uint32_t c2 = nfields; c2 < C; ++c2) {  // fields the record lacks
+        const uint32_t slot = TB.str_slot[c2];
+        if (slot != 0xFF)
+          cols[c2].offsets[r + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
+        else
+          store_value(cols[c2], TB.col_type[c2], r, 0);
+      }
+    };
+    // Converts the numeric field (r, c) that starts at chunk position q.
+    auto convert_at = [&](uint64_t r, uint32_t c, int q) {
+      const uint32_t type = TB.col_type[c];
+      uint8_t buf[kNumericMaxLen + 1];
+      int n = 0;
+      bool ended = false;
+      int p = tid * B + q;
+      const int tend = static_cast<int>(v1 - v0);
+      while (p < tend && !ended && n <= kNumericMaxLen) {
+        const int u = p / B, i = p - u * B;
+        const int span = min(min(64 - (i & 63), B - i), tend - p);
+        const uint64_t dlw = s_dl[u * MW + (i >> 6)] >> (i & 63);
+        const uint64_t dmw = s_dm[u * MW + (i >> 6)] >> (i & 63);
+        const int dpos = dlw ? __ffsll(static_cast<long long>(dlw)) - 1 : 64;
+        const int stop = min(dpos, span);
+        uint64_t bits = dmw & bits_below(stop);
+        while (bits && n <= kNumericMaxLen) {
+          const int j = __ffsll(static_cast<long long>(bits)) - 1;
+          bits &= bits - 1;
+          buf[n++] = s_tile[p + j];
+        }
+        if (dpos < span) ended = true;
+        p += span;
+      }
+      if (!ended && n <= kNumericMaxLen && p >= tend && v1 < VL) {
+        uint32_t s = tile_send;
+        for (uint64_t x = v1; x < VL; ++x) {
+          const uint8_t b = vbase[x];
+          const uint32_t g = TB.group_of[b];
+          const uint32_t tag = (TB.emit[g] >> (2 * s)) & 3u;
+          s = vget(TB.trans[g], s);
+          if (tag == PP_TAG_DATA) {
+            buf[n++] = b;
+            if (n > kNumericMaxLen) break;
+          } else if (tag != PP_TAG_CONTROL) {
+            break;
+          }
+          if (s == TB.invalid_state) break;
+        }
+      }
+      uint64_t val = 0;
+      const int st = n > kNumericMaxLen ? kConvFail : convert_value(type, buf, n, &val);
+      store_value(cols[c], type, r, val);
+      if (st != kConvOk) {
+        const uint32_t bit = 1u << (r & 31);
+        atomicOr(&J.null_bits[TB.num_slot[c] * J.bit_words + (r >> 5)], bit);
+        if (st == kConvFail) atomicOr(&J.fail_bits[r >> 5], bit);
+      }
+    };
+    auto stage_piece = [&](uint32_t slot, int a, int b) {
+      int x = a;
+      while (x < b) {
+        const int rs = next_bit(dm, x, b, true);
+        if (rs >= b) break;
+        const int re = next_bit(dm, rs, b, false);
+        const uint32_t at = H->stage_off[slot] + s_cnt[slot * NT + tid];
+        smem_copy(s_stage + at, chunk + rs, re - rs);
+        s_cnt[slot * NT + tid] = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (re - rs));
+        x = re;
+      }
+    };
+
+    {
+      uint32_t c = col_start;
+      uint64_t r = row_start;
+      int pos = lo;
+      // the input's first field has no delimiter before it
+      if (t == 0 && tid == 0 && J.len > 0 && C > 0 && TB.num_slot[0] != 0xFF && rows_cap > 0)
+        convert_at(0, 0, lo);
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {
+        uint64_t dl = fm[w] | rm[w];
+        while (dl) {
+          const int d = 64 * w + __ffsll(static_cast<long long>(dl)) - 1;
+          dl &= dl - 1;
+          const uint32_t slot = c < C ? TB.str_slot[c] : 0xFFu;
+          if (slot != 0xFF) {
+            stage_piece(slot, pos, d);
+            if (r < rows_cap) cols[c].offsets[r + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
+          }
+          const bool is_rd = (rm[w] >> (d & 63)) & 1ull;
+          if (is_rd) {
+            record_end(r, c + 1 > kColSat ? kColSat : c + 1);
+            ++r;
+            c = 0;
+          } else {
+            c = min(c + 1, kColSat);
+          }
+          const bool at_end = (cv0 + d + 1) >= static_cast<int64_t>(VL);
+          if (c < C && TB.num_slot[c] != 0xFF && r < rows_cap && !(is_rd && at_end))
+            convert_at(r, c, d + 1);
+          pos = d + 1;
+        }
+      }
+      if (c < C && TB.str_slot[c] != 0xFF) stage_piece(TB.str_slot[c], pos, hi);
+
+      // end of input: the trailing record, and the totals
+      if (last_tile && lo < hi && cv0 + hi == static_cast<int64_t>(VL)) {
+        const bool last_rd = test_bit(rm, hi - 1);
+        const bool accept = (TB.accept_mask >> s_end) & 1u;
+        uint64_t rows = r;
+        if (!last_rd && accept) {
+          const uint32_t slot = c < C ? TB.str_slot[c] : 0xFFu;
+          if (slot != 0xFF && r < rows_cap)
+            cols[c].offsets[r + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
+          record_end(r, c + 1 > kColSat ? kColSat : c + 1);
+          rows = r + 1;
+        }
+        J.misc->rows = static_cast<int64_t>(rows);
+        J.misc->final_state = static_cast<int32_t>(s_end);
+        for (uint32_t k = 0; k < NS; ++k) J.misc->bytes_total[k] = H->col_base[k] + H->tile_tot[k];
+        __threadfence();
+        J.misc->done = 1u;
+      }
+    }
+
+    // ----------------------------- write the gathered string bytes (TMA)
+    if (NS > 0) {
+      fence_proxy_async_smem();
+      __syncthreads();
+      for (uint32_t k = 0; k < NS; ++k) {
+        const Col& col = cols[H->str_col[k]];
+        const uint64_t cap = col.values_cap;
+        const uint64_t c0 = static_cast<uint64_t>(H->col_base[k]);
+        const uint64_t c1 = min(c0 + H->tile_tot[k], cap);
+        if (c1 <= c0) continue;
+        uint8_t* gbase = static_cast<uint8_t*>(col.values);
+        const uintptr_t g0 = reinterpret_cast<uintptr_t>(gbase + c0);
+        const uintptr_t g1 = reinterpret_cast<uintptr_t>(gbase + c1);
+        const uintptr_t A = (g0 + 15) & ~uintptr_t(15), Bn = g1 & ~uintptr_t(15);
+        const uint8_t* sbase = s_stage + H->stage_off[k];
+        if (tid == 0 && Bn > A) {
+          tma_store_1d(reinterpret_cast<void*>(A), sbase + (A - g0), static_cast<uint32_t>(Bn - A));
+          pending_store = true;
+        }
+        if (tid < 32) {
+          const uintptr_t x = tid < 16 ? g0 + tid : max(Bn, A) + (tid - 16);
+          const bool ok = tid < 16 ? (x < A && x < g1) : (x < g1);
+          if (ok) *reinterpret_cast<uint8_t*>(x) = sbase[x - g0];
+        }
+      }
+      if (tid == 0 && pending_store) bulk_commit();
+    }
+    __syncthreads();
+  }
+  if (tid == 0) bulk_wait_all();
+}
+
+}  // namespace pp

@@ -1,0 +1,21 @@
+// pp_launch.h -- host-side view of the compiled tile shapes.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace pp {
+
+struct ShapeInfo {
+  int threads = 0;
+  int tile_bytes = 0;
+  size_t smem_bytes = 0;
+  const void* (*kernel)(int nspec) = nullptr;  // pp_tile_kernel<Shape, NSPEC>
+};
+
+// tile configurations selectable with PP_OPT_TILE_CONFIG
+ShapeInfo shape_info_tiny();    // 32 threads x 16 B   =   512 B tiles
+ShapeInfo shape_info_small();   // 64 threads x 48 B   =  3 KiB tiles
+ShapeInfo shape_info_mid();     // 256 threads x 112 B = 28 KiB tiles
+ShapeInfo shape_info_wide();    // 128 threads x 208 B = 26 KiB tiles
+
+}  // namespace pp

@@ -1,0 +1,3 @@
+// Tile shape "mid": 256 threads x 112 bytes per thread.
+#include "pp_tile_inst.cuh"
+PP_DEFINE_SHAPE(mid, 256, 7)

@@ -1,0 +1,3 @@
+// Tile shape "small": 64 threads x 48 bytes per thread.
+#include "pp_tile_inst.cuh"
+PP_DEFINE_SHAPE(small, 64, 3)

@@ -1,0 +1,3 @@
+// Tile shape "tiny": 32 threads x 16 bytes per thread.
+#include "pp_tile_inst.cuh"
+PP_DEFINE_SHAPE(tiny, 32, 1)

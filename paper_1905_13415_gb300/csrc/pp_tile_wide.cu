@@ -1,0 +1,3 @@
+// Tile shape "wide": 128 threads x 208 bytes per thread.
+#include "pp_tile_inst.cuh"
+PP_DEFINE_SHAPE(wide, 128, 13)

@@ -1,0 +1,49 @@
+"""Shared helpers for the GPU parity tests: run a parse through the C ABI
+and compare it element by element with the oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+
+OTYPE = {"string": O.STRING, "int32": O.INT32, "int64": O.INT64, "float64": O.FLOAT64,
+         "timestamp": O.TIMESTAMP_S, "date": O.DATE_D, "timestamp_clf": O.TIMESTAMP_CLF}
+
+
+def oracle_format(name: str):
+    return O.csv6() if name == "csv" else O.log8()
+
+
+def oracle_parse(dialect: str, schema, raw: bytes):
+    return O.parse(oracle_format(dialect), [OTYPE[t] if isinstance(t, str) else t for t in schema], raw)
+
+
+def assert_same(got_host: dict, res, ref, rows_cap: int | None = None, what=""):
+    """Every output of the GPU parse equals the oracle's: status, counts,
+    offsets, value bytes, fixed-width values, validity and row_valid."""
+    assert res.status == ref.status, (what, res, ref.status)
+    assert res.rows == ref.rows, (what, res.rows, ref.rows)
+    assert res.first_invalid_offset == ref.first_invalid_offset, (what, res.first_invalid_offset,
+                                                                  ref.first_invalid_offset)
+    assert res.final_state == ref.final_state, (what, res.final_state, ref.final_state)
+    rows = ref.rows if rows_cap is None else min(ref.rows, rows_cap)
+    if rows_cap is None or ref.rows <= rows_cap:
+        assert res.n_rejected == ref.n_rejected, (what, res.n_rejected, ref.n_rejected)
+    nb = (rows + 7) // 8
+    for c, col in enumerate(ref.columns):
+        g = got_host["columns"][c]
+        if col.offsets is not None:
+            assert res.values_bytes_needed[c] == col.bytes_total, (what, c)
+            assert np.array_equal(g["offsets"][: rows + 1], col.offsets[: rows + 1]), (what, c, "offsets")
+            end = int(col.offsets[rows])
+            assert np.array_equal(g["values"][:end], col.values[:end]), (what, c, "bytes")
+        else:
+            assert np.array_equal(g["values"][:rows].view(np.uint8), col.values[:rows].view(np.uint8)), \
+                (what, c, "values", first_diff(g["values"][:rows], col.values[:rows]))
+        assert np.array_equal(g["validity"][:nb], col.validity[:nb]), (what, c, "validity")
+    assert np.array_equal(got_host["row_valid"][:nb], ref.row_valid[:nb]), (what, "row_valid")
+
+
+def first_diff(a, b):
+    idx = np.nonzero(a != b)[0]
+    return None if len(idx) == 0 else (int(idx[0]), a[idx[0]], b[idx[0]])

@@ -1,0 +1,144 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/parparaw.h declares; create() validates tables on the host (no GPU
+needed); the package's format tables agree with the oracle's."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_1905_13415_gb300 import build
+
+    build.build()
+    from paper_1905_13415_gb300 import _abi
+
+    return _abi
+
+
+def declared_entry_points():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            names |= set(re.findall(r"\b(parparaw_\w+)\s*\(", open(os.path.join(inc, f)).read()))
+    return names
+
+
+def test_exports_every_declared_symbol(abi):
+    lib = abi.load()
+    declared = declared_entry_points()
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(abi.EXPORTED)
+
+
+def test_status_strings(abi):
+    for code in range(-9, 1):
+        assert abi.status_string(code) and abi.status_string(code) != "unknown status"
+    assert abi.status_string(-42) == "unknown status"
+
+
+def _create(abi, fmt, schema):
+    from paper_1905_13415_gb300 import Parser
+
+    return Parser(fmt, schema)
+
+
+def test_create_and_info(abi):
+    from paper_1905_13415_gb300 import formats
+
+    p = _create(abi, formats.rfc4180_csv(), ["int32", "string", "float64", "string"])
+    info = p.info()
+    assert (info.num_states, info.num_groups, info.num_symbols) == (6, 5, 4)
+    assert (info.num_columns, info.num_string_columns) == (4, 2)
+    assert info.catch_all_idempotent == 1
+    assert info.tile_bytes > 0 and info.threads_per_block > 0
+    for cfg, tile in [(1, 512), (2, 3072), (3, 28672), (4, 26624)]:
+        p.set_option(abi.OPT_TILE_CONFIG, cfg)
+        assert p.info().tile_bytes == tile
+    p.close()
+
+
+def test_create_rejects_bad_tables(abi):
+    from paper_1905_13415_gb300 import ParparawError, formats
+
+    good = formats.rfc4180_csv()
+
+    def variant(**kw):
+        d = dict(name="x", transitions=good.transitions.copy(), emit=good.emit.copy(), symbols=good.symbols,
+                 groups=list(good.groups), catch_all=good.catch_all, start_state=good.start_state,
+                 invalid_state=good.invalid_state, accept_states=list(good.accept_states))
+        d.update(kw)
+        return formats.Format(**d)
+
+    bad_next = good.transitions.copy()
+    bad_next[0, 0] = 6
+    not_absorbing = good.transitions.copy()
+    not_absorbing[1, 5] = 0
+    emits_in_inv = good.emit.copy()
+    emits_in_inv[4, 5] = 0
+    cases = [
+        (variant(transitions=bad_next), ["string"], abi.E_BAD_TABLE),
+        (variant(transitions=not_absorbing), ["string"], abi.E_BAD_TABLE),
+        (variant(emit=emits_in_inv), ["string"], abi.E_BAD_TABLE),
+        (variant(symbols=b'\n\n,\r', groups=[0, 1, 2, 3]), ["string"], abi.E_BAD_TABLE),
+        (variant(groups=[0, 1, 2, 4]), ["string"], abi.E_BAD_TABLE),
+        (variant(start_state=9), ["string"], abi.E_BAD_TABLE),
+        (good, [99], abi.E_BAD_TABLE),
+        (good, ["string"] * 17, abi.E_UNSUPPORTED),
+        (good, ["int32"] * 65, abi.E_UNSUPPORTED),
+    ]
+    for fmt, schema, code in cases:
+        with pytest.raises(ParparawError) as e:
+            _create(abi, fmt, schema)
+        assert e.value.code == code, (schema, code)
+
+
+def test_non_idempotent_catch_all_is_flagged(abi):
+    from paper_1905_13415_gb300 import formats
+
+    tr = np.array([[0, 0], [1, 0]], np.uint8)  # catch-all toggles between two states
+    em = np.zeros((2, 2), np.uint8)
+    fmt = formats.Format("toggle", tr, em, b"\n", [0], 1, 0, 0xFF, [0, 1])
+    assert _create(abi, fmt, ["string"]).info().catch_all_idempotent == 0
+
+
+@pytest.mark.parametrize("name", ["csv", "log"])
+def test_package_formats_match_oracle_formats(name):
+    from paper_1905_13415_gb300 import formats
+
+    f = formats.by_name(name)
+    o = O.csv6() if name == "csv" else O.log8()
+    assert f.num_states == o.num_states and f.num_groups == o.num_groups
+    assert np.array_equal(f.transitions, o.next) and np.array_equal(f.emit, o.emit)
+    assert f.start_state == o.start_state and f.invalid_state == o.invalid_state
+    assert f.accept_mask == o.accept_mask
+    for b in range(256):
+        g = f.groups[f.symbols.index(bytes([b]))] if bytes([b]) in f.symbols else f.catch_all
+        assert g == o.group_of(b)
+
+
+def test_parse_rejects_bad_arguments_without_gpu(abi):
+    from paper_1905_13415_gb300 import formats
+
+    lib = abi.load()
+    p = _create(abi, formats.rfc4180_csv(), ["string"])
+    desc = abi.pp_columns()
+    desc.num_columns = 2  # schema has one column
+    rc = lib.parparaw_parse(p.handle, None, 0, ctypes.byref(desc), None)
+    assert rc == abi.E_ARG
+    rc = lib.parparaw_parse(None, None, 0, ctypes.byref(desc), None)
+    assert rc == abi.E_ARG
+    assert lib.parparaw_parse_batch(None, 1, None) == abi.E_ARG
+    assert lib.parparaw_parse_batch(None, 0, None) == abi.OK

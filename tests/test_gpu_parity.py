@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, element by
+element (bit-exact: the whole output is integer / byte data, and floats are
+correctly rounded on both sides).
+
+Tile configurations 1 (512 B) and 2 (3 KiB) put tile and chunk boundaries
+inside every construct; 0 is the default shape used by the benchmark."""
+from __future__ import annotations
+
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from parity import assert_same, oracle_parse
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+CONFIGS = [1, 2, 3, 4]
+
+
+@pytest.fixture(scope="module")
+def pp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1905_13415_gb300 as pkg
+
+    return pkg
+
+
+def to_dev(raw: bytes, offset: int = 0):
+    buf = torch.zeros(len(raw) + offset + 16, dtype=torch.uint8)
+    buf[offset: offset + len(raw)] = torch.frombuffer(bytearray(raw), dtype=torch.uint8) if raw else buf[:0]
+    d = buf.to("cuda")
+    return d[offset: offset + len(raw)]
+
+
+def run(pp, dialect, schema, raw, cfg, offset=0, rows_cap=None, caps=None):
+    p = pp.Parser(pp.formats.by_name(dialect), schema, tile_config=cfg)
+    data = to_dev(raw, offset)
+    if rows_cap is None and caps is None:
+        out, res = p.parse(data)
+    else:
+        out = p.allocate(rows_cap, caps)
+        p.parse_into(data, out)
+        res = out.result()
+    torch.cuda.synchronize()
+    rows = min(res.rows, out.rows_cap)
+    return out.to_host(rows), res
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_worked_examples(pp, cfg):
+    cases = json.load(open(os.path.join(GOLD, "worked_examples.json")))["cases"]
+    for case in cases:
+        raw = case["input"].encode()
+        schema = ["string"] * case["columns"]
+        got, res = run(pp, case["dialect"], schema, raw, cfg)
+        assert_same(got, res, oracle_parse(case["dialect"], schema, raw), what=case["input"])
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_random_small_inputs(pp, cfg):
+    rng = random.Random(cfg)
+    for it in range(300):
+        n = rng.randint(0, 1200)
+        alphabet = b'\n,"\rab' if it % 2 else b'\n,"ab1.'
+        raw = bytes(rng.choice(alphabet) for _ in range(n))
+        ncol = rng.randint(1, 4)
+        schema = [rng.choice(["string", "string", "int32", "float64"]) for _ in range(ncol)]
+        got, res = run(pp, "csv", schema, raw, cfg)
+        assert_same(got, res, oracle_parse("csv", schema, raw), what=(it, raw[:80]))
+
+
+@pytest.mark.parametrize("workload,nrows", [("mixed", 2500), ("trip", 3000), ("review", 300), ("log", 3000)])
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_generated_workloads(pp, workload, nrows, cfg):
+    raw, _ = synth.records(workload, synth.BASE_SEED + 7, 0, nrows)
+    schema = synth.SCHEMAS[workload]
+    got, res = run(pp, synth.DIALECT[workload], schema, raw, cfg)
+    ref = oracle_parse(synth.DIALECT[workload], schema, raw)
+    assert ref.rows == nrows and res.status == O.OK
+    assert_same(got, res, ref, what=workload)
+
+
+@pytest.mark.parametrize("offset", [1, 3, 7, 15])
+def test_unaligned_input(pp, offset):
+    raw, _ = synth.records("mixed", 5, 0, 500)
+    schema = synth.SCHEMAS["mixed"]
+    for cfg in (1, 3):
+        got, res = run(pp, "csv", schema, raw, cfg, offset=offset)
+        assert_same(got, res, oracle_parse("csv", schema, raw), what=(offset, cfg))
+
+
+def test_empty_and_tiny(pp):
+    for raw in [b"", b"\n", b"a", b",", b'"', b"\r\n", b"x" * 17]:
+        for cfg in (1, 3):
+            got, res = run(pp, "csv", ["string", "string"], raw, cfg)
+            assert_same(got, res, oracle_parse("csv", ["string", "string"], raw), what=raw)
+
+
+def test_invalid_in_the_middle(pp):
+    raw, _ = synth.records("mixed", 9, 0, 2000)
+    schema = synth.SCHEMAS["mixed"]
+    bad = bytearray(raw)
+    cut = len(bad) // 2
+    while bad[cut] != ord("\n"):
+        cut += 1
+    bad[cut + 1: cut + 1] = b'ab"c,'
+    for cfg in (1, 2, 3):
+        got, res = run(pp, "csv", schema, bytes(bad), cfg)
+        ref = oracle_parse("csv", schema, bytes(bad))
+        assert ref.status == O.E_INVALID_INPUT
+        assert_same(got, res, ref, what=cfg)
+
+
+def test_rejects_and_nulls(pp):
+    raw = b"1,a,2.5\n,b,\nx,c,1\n4,d\n5,e,6,7\n99999999999,f,1e3\n-7,\"g\"\"h\",-0.0\n"
+    schema = ["int32", "string", "float64"]
+    for cfg in CONFIGS:
+        got, res = run(pp, "csv", schema, raw, cfg)
+        assert_same(got, res, oracle_parse("csv", schema, raw), what=cfg)
+
+
+def test_capacity(pp):
+    raw, _ = synth.records("mixed", 3, 0, 1000)
+    schema = synth.SCHEMAS["mixed"]
+    ref = oracle_parse("csv", schema, raw)
+    # too few rows: exact row count reported, nothing written past the caps
+    got, res = run(pp, "csv", schema, raw, 3, rows_cap=100, caps=[len(raw)] * len(schema))
+    assert res.status == O.__dict__.get("E_CAPACITY", -6) and res.rows == ref.rows
+    assert_same_prefix = min(100, ref.rows)
+    for c, col in enumerate(ref.columns):
+        if col.offsets is not None:
+            assert np.array_equal(got["columns"][c]["offsets"][: assert_same_prefix + 1],
+                                  col.offsets[: assert_same_prefix + 1])
+    # too few string bytes: exact byte counts reported
+    got, res = run(pp, "csv", schema, raw, 3, rows_cap=ref.rows, caps=[10] * len(schema))
+    assert res.status == -6
+    for c, col in enumerate(ref.columns):
+        if col.offsets is not None:
+            assert res.values_bytes_needed[c] == col.bytes_total
+
+
+def _random_dfa(rng, S, G, with_inv):
+    inv = S - 1 if with_inv else 0xFF
+    tr = np.zeros((G, S), np.uint8)
+    em = np.zeros((G, S), np.uint8)
+    for g in range(G):
+        for s in range(S):
+            if with_inv and s == inv:
+                tr[g, s], em[g, s] = inv, 3
+            else:
+                tr[g, s] = rng.randrange(S)
+                em[g, s] = rng.choice([0, 0, 0, 1, 2, 3])
+    return tr, em, inv
+
+
+def test_random_dfas(pp):
+    """Arbitrary DFAs (idempotent catch-all or not) give the oracle's result."""
+    rng = random.Random(11)
+    for it in range(60):
+        S = rng.randint(1, 8)
+        G = rng.randint(2, 7)
+        with_inv = S > 1 and rng.random() < 0.5
+        tr, em, inv = _random_dfa(rng, S, G, with_inv)
+        if it % 3 == 0:  # make the catch-all (last group) idempotent
+            for s in range(S):
+                tr[G - 1, s] = tr[G - 1, tr[G - 1, s]]
+        syms = bytes(rng.sample(range(256), G - 1))
+        accept = [s for s in range(S) if rng.random() < 0.7]
+        fmt = pp.formats.Format("rand", tr, em, syms, list(range(G - 1)), G - 1, rng.randrange(S), inv, accept)
+        ofmt = O.Format(S, G, tr, em, syms, list(range(G - 1)), G - 1, fmt.start_state, inv, fmt.accept_mask)
+        alphabet = list(syms) + [ord("q"), ord("z")]
+        raw = bytes(rng.choice(alphabet) for _ in range(rng.randint(0, 3000)))
+        schema = ["string"] * rng.randint(1, 3)
+        p = pp.Parser(fmt, schema, tile_config=rng.choice([1, 2, 3]))
+        out, res = p.parse(to_dev(raw))
+        torch.cuda.synchronize()
+        ref = O.parse(ofmt, [O.STRING] * len(schema), raw)
+        assert_same(out.to_host(min(res.rows, out.rows_cap)), res, ref, what=(it, S, G))
+
+
+def test_batch_mixed_formats(pp):
+    items, refs = [], []
+    rng = random.Random(5)
+    for i in range(12):
+        wl = ["mixed", "log", "review", "trip"][i % 4]
+        raw, _ = synth.records(wl, 100 + i, 0, rng.randint(1, 400))
+        schema = synth.SCHEMAS[wl]
+        p = pp.Parser(pp.formats.by_name(synth.DIALECT[wl]), schema, tile_config=2)
+        data = to_dev(raw, offset=i % 5)
+        ref = oracle_parse(synth.DIALECT[wl], schema, raw)
+        out = p.allocate(max(ref.rows, 1), [max(len(raw), 1)] * len(schema))
+        items.append((p, data, out))
+        refs.append(ref)
+    pp.parse_batch(items)
+    torch.cuda.synchronize()
+    for (p, data, out), ref in zip(items, refs):
+        res = out.result()
+        assert_same(out.to_host(res.rows), res, ref, what="batch")
