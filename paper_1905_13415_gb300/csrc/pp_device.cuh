@@ -117,6 +117,7 @@ __device__ __forceinline__ uint64_t bit_range(int lo, int hi) {
 
 constexpr uint64_t kIdentityVec = 0x0706050403020100ull;
 
+// entries e0..e3 (bytes) -> nibbles in bits 0..15; bits 16..31 are not defined
 __device__ __forceinline__ uint32_t nibble_selector(uint32_t bytes4) {
   uint32_t y = bytes4 | (bytes4 >> 4);  // byte0 = e0 | e1<<4, byte2 = e2 | e3<<4
   return __byte_perm(y, 0u, 0x0020u);
@@ -132,7 +133,7 @@ __device__ __forceinline__ uint32_t vget(uint64_t v, uint32_t i) {
 }
 // 32-bit nibble form of a vector, for status words
 __device__ __forceinline__ uint32_t vpack(uint64_t v) {
-  return nibble_selector(static_cast<uint32_t>(v)) |
+  return (nibble_selector(static_cast<uint32_t>(v)) & 0xFFFFu) |
          (nibble_selector(static_cast<uint32_t>(v >> 32)) << 16);
 }
 __device__ __forceinline__ uint32_t nib4_to_bytes(uint32_t x) {
