@@ -76,7 +76,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libparparaw.so")
+    """The in-tree library; PARPARAW_LIBRARY may name a profiling build of it."""
+    return os.environ.get("PARPARAW_LIBRARY") or os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                                "libparparaw.so")
 
 
 def load():

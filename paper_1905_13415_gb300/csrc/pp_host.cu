@@ -40,8 +40,9 @@ __global__ void pp_init_kernel(const __grid_constant__ Launch L) {
     for (uint64_t i = i0; i < J.ntiles; i += stride) {
       J.st_state[i] = 0;
       J.st_rc[i] = 0;
-      J.st_bytes_flag[i] = 0;
     }
+    const uint64_t nb = J.ntiles * TB.num_str;
+    for (uint64_t i = i0; i < nb; i += stride) J.st_bytes[i] = 0;
     const uint64_t nbits = J.bit_words * (1 + static_cast<uint64_t>(TB.num_num));
     for (uint64_t i = i0; i < nbits; i += stride) {
       if (i < J.bit_words) J.fail_bits[i] = 0;
@@ -146,6 +147,9 @@ ShapeInfo shape_for(int cfg) {
     case 2: return shape_info_small();
     case 3: return shape_info_mid();
     case 4: return shape_info_wide();
+    case 5: return shape_info_m128();
+    case 6: return shape_info_m128x6();
+    case 7: return shape_info_s128();
     default: return shape_info_mid();
   }
 }
@@ -208,7 +212,7 @@ bool column_ok(const pp_column& c, uint32_t type) {
 
 // Scratch of one job, carved from one stream-ordered allocation.
 struct ScratchPlan {
-  size_t st_state, st_rc, st_flag, st_agg, st_inc, fail, null_, misc, total;
+  size_t st_state, st_rc, st_bytes, fail, null_, misc, total;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -219,9 +223,7 @@ ScratchPlan plan_scratch(size_t base, uint64_t ntiles, uint32_t ns, uint32_t nn,
   p.misc = o; o = align_up(o + sizeof(Misc), 256);
   p.st_state = o; o = align_up(o + 8 * ntiles, 256);
   p.st_rc = o; o = align_up(o + 8 * ntiles, 256);
-  p.st_flag = o; o = align_up(o + 4 * ntiles, 256);
-  p.st_agg = o; o = align_up(o + 8 * ntiles * ns, 256);
-  p.st_inc = o; o = align_up(o + 8 * ntiles * ns, 256);
+  p.st_bytes = o; o = align_up(o + 8 * ntiles * ns, 256);
   p.fail = o; o = align_up(o + 4 * bit_words, 256);
   p.null_ = o; o = align_up(o + 4 * bit_words * nn, 256);
   p.total = o;
@@ -232,9 +234,7 @@ void fill_job(Job& J, const ScratchPlan& p, uint8_t* scratch) {
   J.misc = reinterpret_cast<Misc*>(scratch + p.misc);
   J.st_state = reinterpret_cast<uint64_t*>(scratch + p.st_state);
   J.st_rc = reinterpret_cast<uint64_t*>(scratch + p.st_rc);
-  J.st_bytes_flag = reinterpret_cast<uint32_t*>(scratch + p.st_flag);
-  J.st_bytes_agg = reinterpret_cast<int64_t*>(scratch + p.st_agg);
-  J.st_bytes_inc = reinterpret_cast<int64_t*>(scratch + p.st_inc);
+  J.st_bytes = reinterpret_cast<uint64_t*>(scratch + p.st_bytes);
   J.fail_bits = reinterpret_cast<uint32_t*>(scratch + p.fail);
   J.null_bits = reinterpret_cast<uint32_t*>(scratch + p.null_);
 }
@@ -253,6 +253,11 @@ pp_status map_err(cudaError_t e) {
   return PP_E_CUDA;
 }
 
+#ifdef PP_PHASE_TIMING
+unsigned long long* g_phase_cycles = nullptr;  // profiling builds: per-phase cycle totals
+int g_last_grid = 0, g_last_per_sm = 0;
+#endif
+
 // Launches init, tile and finalize kernels for a prepared launch.
 pp_status run_launch(Launch& L, const ShapeInfo& shape, int nspec, int64_t grid_limit,
                      const pp_parser* timing, cudaStream_t stream, uint32_t max_jobs_y,
@@ -269,6 +274,13 @@ pp_status run_launch(Launch& L, const ShapeInfo& shape, int nspec, int64_t grid_
   pp_init_kernel<<<dim3(gx_init, gy), kBlockInit, 0, stream>>>(L);
   if ((e = cudaGetLastError()) != cudaSuccess) return map_err(e);
 
+#ifdef PP_PHASE_TIMING
+  if (g_phase_cycles == nullptr) {
+    cudaMalloc(reinterpret_cast<void**>(&g_phase_cycles), 16 * sizeof(unsigned long long));
+    cudaMemset(g_phase_cycles, 0, 16 * sizeof(unsigned long long));
+  }
+  L.phase_cycles = g_phase_cycles;
+#endif
   if (L.total_tiles > 0) {
     const void* kern = shape.kernel(nspec);
     int per_sm = 0;
@@ -276,6 +288,10 @@ pp_status run_launch(Launch& L, const ShapeInfo& shape, int nspec, int64_t grid_
       return map_err(e);
     uint64_t grid = std::min<uint64_t>(L.total_tiles, static_cast<uint64_t>(per_sm) * props.sms);
     if (grid_limit > 0) grid = std::min<uint64_t>(grid, static_cast<uint64_t>(grid_limit));
+#ifdef PP_PHASE_TIMING
+    g_last_grid = static_cast<int>(grid);
+    g_last_per_sm = per_sm;
+#endif
     if (timing && timing->ev_start) cudaEventRecord(timing->ev_start, stream);
     void* args[] = {&L};
     e = cudaLaunchKernel(kern, dim3(static_cast<uint32_t>(grid)), dim3(shape.threads), args,
@@ -297,6 +313,23 @@ pp_status run_launch(Launch& L, const ShapeInfo& shape, int nspec, int64_t grid_
 using namespace pp;
 
 // ============================================================== the ABI ===
+
+#ifdef PP_PHASE_TIMING
+// Profiling builds only (not part of include/parparaw.h): copies the
+// accumulated per-phase cycle totals of the tile kernel to out[0..9].
+extern "C" int parparaw_debug_phase_cycles(unsigned long long* out, int reset) {
+  if (g_phase_cycles == nullptr) return -1;
+  cudaDeviceSynchronize();
+  cudaMemcpy(out, g_phase_cycles, 10 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (reset) cudaMemset(g_phase_cycles, 0, 16 * sizeof(unsigned long long));
+  return 0;
+}
+extern "C" int parparaw_debug_last_launch(int* grid, int* per_sm) {
+  *grid = g_last_grid;
+  *per_sm = g_last_per_sm;
+  return 0;
+}
+#endif
 
 extern "C" const char* parparaw_status_string(int status) {
   switch (status) {
@@ -420,7 +453,7 @@ extern "C" pp_status parparaw_set_option(pp_parser* P, pp_option option, int64_t
   if (P == nullptr) return PP_E_ARG;
   switch (option) {
     case PP_OPT_TILE_CONFIG:
-      if (value < 0 || value > 4) return PP_E_ARG;
+      if (value < 0 || value > 7) return PP_E_ARG;
       P->tile_config = static_cast<int>(value);
       return PP_OK;
     case PP_OPT_TIMEOUT_MS:

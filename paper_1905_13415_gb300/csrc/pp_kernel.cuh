@@ -37,17 +37,38 @@
 #include "pp_device.cuh"
 #include "pp_types.h"
 
+// Opt-in instrumentation (profiling builds only, -DPP_PHASE_TIMING): thread 0
+// accumulates the cycles between block-wide synchronisation points per phase.
+#ifdef PP_PHASE_TIMING
+#define PP_PHASE(k)                        \
+  do {                                     \
+    if (tid == 0) {                        \
+      const long long _now = clock64();    \
+      H->ph_cycles[k] += _now - ph_last;   \
+      ph_last = _now;                      \
+    }                                      \
+  } while (0)
+#else
+#define PP_PHASE(k) \
+  do {              \
+  } while (0)
+#endif
+
 namespace pp {
 
-template <int NT_, int VPT_>
+template <int NT_, int VPT_, int MINB_ = 1>
 struct TileShape {
   static constexpr int NT = NT_;
   static constexpr int VPT = VPT_;
+  static constexpr int MINB = MINB_;       // resident blocks per SM asked of ptxas
   static constexpr int B = 16 * VPT;       // bytes per thread (chunk)
   static constexpr int T = NT * B;         // bytes per tile
   static constexpr int MW = (B + 63) / 64; // 64-bit mask words per chunk
   static constexpr int NW = NT / 32;
   static constexpr int kStage = T + 32 * PP_MAX_STRING_COLUMNS + 64;
+  // numeric fields queued per tile for the block-wide conversion pass; a tile
+  // with more falls back to converting the rest inline
+  static constexpr int kConvCap = T / 8;
 };
 
 struct SmemHead {
@@ -65,6 +86,11 @@ struct SmemHead {
   uint32_t wsumk[PP_MAX_STRING_COLUMNS / 2][32];
   Tables tab;
   uint8_t str_col[PP_MAX_STRING_COLUMNS];  // slot -> column
+  int32_t job_loaded;
+  uint32_t nconv;
+  long long ph_cycles[10];  // profiling builds only
+  Job jd;                  // the current job and its columns, staged from the
+  Col cd[PP_MAX_COLUMNS];  // launch parameters / global memory once per job
 };
 
 template <class Shape>
@@ -75,7 +101,9 @@ struct SmemLayout {
   static constexpr size_t kDm = kStage + ((Shape::kStage + 127) & ~size_t(127));
   static constexpr size_t kDl = kDm + sizeof(uint64_t) * Shape::NT * Shape::MW;
   static constexpr size_t kCnt = kDl + sizeof(uint64_t) * Shape::NT * Shape::MW;
-  static constexpr size_t kBytes = kCnt + sizeof(uint16_t) * Shape::NT * PP_MAX_STRING_COLUMNS;
+  static constexpr size_t kConvA = kCnt + sizeof(uint16_t) * Shape::NT * PP_MAX_STRING_COLUMNS;
+  static constexpr size_t kConvB = kConvA + sizeof(uint32_t) * Shape::kConvCap;
+  static constexpr size_t kBytes = kConvB + sizeof(uint16_t) * Shape::kConvCap;
 };
 
 // ---------------------------------------------------- look-back (1 word) ---
@@ -95,39 +123,56 @@ struct RcPolicy {  // chain 2: records and column offsets
   static constexpr uint64_t kIdentity = 0;
 };
 
+// How many lanes of a look-back window (lane i = tile idx - i) can be
+// combined: up to and including the nearest inclusive prefix, as soon as
+// every lane before it has published; 32 when all published without an
+// inclusive prefix; 0 while the window must wait.  *done: an inclusive
+// prefix was reached.
+__device__ __forceinline__ int window_take(uint32_t valid, uint32_t inc, bool* done) {
+  const int fi = valid == 0xffffffffu ? 32 : __ffs(~valid) - 1;
+  const int fc = inc ? __ffs(inc) - 1 : 32;
+  *done = fc < fi;
+  if (fc < fi) return fc + 1;
+  return fi == 32 ? 32 : 0;
+}
+
 // Called by one full warp.  Publishes the tile's aggregate, walks back over
 // predecessors (32 at a time) until an inclusive prefix is found, publishes
 // the tile's inclusive prefix and returns the exclusive one.  `first` is the
-// prefix of tile 0.
+// prefix of tile 0.  All waits end at `deadline` (then PP_E_TIMEOUT).
 template <class P>
 __device__ uint64_t lookback_word(uint64_t* st, uint64_t t, uint64_t agg, uint64_t first,
                                   uint64_t deadline, Misc* misc) {
   const int lane = threadIdx.x & 31;
+  // flag and payload share one 64-bit word, so relaxed accesses suffice
   if (t == 0) {
-    if (lane == 0) st_release_u64(&st[0], kFlagInc | P::to_word(P::combine(first, agg)));
+    if (lane == 0) st_relaxed_u64(&st[0], kFlagInc | P::to_word(P::combine(first, agg)));
     return first;
   }
-  if (lane == 0) st_release_u64(&st[t], kFlagAgg | P::to_word(agg));
+  if (lane == 0) st_relaxed_u64(&st[t], kFlagAgg | P::to_word(agg));
   uint64_t acc = P::kIdentity;
   int64_t idx = static_cast<int64_t>(t) - 1;
   for (;;) {
     const int64_t mine = idx - lane;
-    uint64_t w = kFlagInc | P::to_word(P::kIdentity);
-    if (mine >= 0) {
-      w = ld_acquire_u64(&st[mine]);
-      while ((w & kFlagMask) == 0) {
-        if (globaltimer_ns() > deadline) {
-          atomicOr(&misc->timeout, 1u);
-          w = kFlagInc | P::to_word(P::kIdentity);
-          break;
-        }
-        __nanosleep(32);
-        w = ld_acquire_u64(&st[mine]);
+    uint64_t w = kFlagInc | P::to_word(P::kIdentity);  // before tile 0
+    if (mine >= 0) w = ld_relaxed_u64(&st[mine]);
+    bool done = false;
+    int take;
+    for (;;) {
+      take = window_take(__ballot_sync(0xffffffffu, (w & kFlagMask) != 0),
+                         __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagInc), &done);
+      if (take > 0) break;
+      const bool expired = __shfl_sync(0xffffffffu, globaltimer_ns() > deadline ? 1 : 0, 0) != 0;
+      if (expired) {
+        if (lane == 0) atomicOr(&misc->timeout, 1u);
+        done = true;
+        take = 0;
+        break;
       }
+      __nanosleep(20);
+      if ((w & kFlagMask) == 0) w = ld_relaxed_u64(&st[mine]);
     }
-    const uint32_t incmask = __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagInc);
-    const int firstinc = incmask ? __ffs(incmask) - 1 : 32;
-    uint64_t v = lane <= firstinc ? P::from_word(w) : P::kIdentity;
+    uint64_t v = lane < take ? P::from_word(w) : P::kIdentity;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const uint64_t o = __shfl_down_sync(0xffffffffu, v, off);
@@ -135,10 +180,10 @@ __device__ uint64_t lookback_word(uint64_t* st, uint64_t t, uint64_t agg, uint64
     }
     v = __shfl_sync(0xffffffffu, v, 0);
     acc = P::combine(v, acc);
-    if (incmask) break;
+    if (done) break;
     idx -= 32;
   }
-  if (lane == 0) st_release_u64(&st[t], kFlagInc | P::to_word(P::combine(acc, agg)));
+  if (lane == 0) st_relaxed_u64(&st[t], kFlagInc | P::to_word(P::combine(acc, agg)));
   return acc;
 }
 
@@ -174,6 +219,31 @@ __device__ __forceinline__ bool test_bit(const uint64_t (&m)[MW], int p) {
     if ((p >> 6) == w) r = (m[w] >> (p & 63)) & 1ull;
   return r;
 }
+
+// Ascending iteration over the set bits of a chunk mask without unrolling the
+// loop body per mask word: the words shift down as they are exhausted.
+template <int MW>
+struct BitIter {
+  uint64_t w[MW];
+  int base;
+  __device__ __forceinline__ explicit BitIter(const uint64_t (&m)[MW]) : base(0) {
+#pragma unroll
+    for (int i = 0; i < MW; ++i) w[i] = m[i];
+  }
+  // next set position, or -1
+  __device__ __forceinline__ int next() {
+    while (w[0] == 0) {
+      if (base + 64 >= 64 * MW) return -1;
+#pragma unroll
+      for (int i = 0; i + 1 < MW; ++i) w[i] = w[i + 1];
+      w[MW - 1] = 0;
+      base += 64;
+    }
+    const int p = base + __ffsll(static_cast<long long>(w[0])) - 1;
+    w[0] &= w[0] - 1;
+    return p;
+  }
+};
 
 // shared -> shared byte copy with 32-bit stores where the destination allows
 __device__ __forceinline__ void smem_copy(uint8_t* dst, const uint8_t* src, int n) {
@@ -213,7 +283,7 @@ __device__ __forceinline__ void store_value(const Col& col, uint32_t type, uint6
 // ------------------------------------------------------------- kernel ---
 
 template <class Shape, int NSPEC>
-__global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constant__ Launch L) {
+__global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const __grid_constant__ Launch L) {
   constexpr int NT = Shape::NT, VPT = Shape::VPT, B = Shape::B, T = Shape::T, MW = Shape::MW;
   using Lay = SmemLayout<Shape>;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -223,6 +293,8 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
   uint64_t* s_dm = reinterpret_cast<uint64_t*>(smem + Lay::kDm);
   uint64_t* s_dl = reinterpret_cast<uint64_t*>(smem + Lay::kDl);
   uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + Lay::kCnt);
+  uint32_t* s_conv_a = reinterpret_cast<uint32_t*>(smem + Lay::kConvA);  // start | column << 16
+  uint16_t* s_conv_b = reinterpret_cast<uint16_t*>(smem + Lay::kConvB);  // row - first row of tile
   const Tables& TB = H->tab;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -230,15 +302,19 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
     mbar_init(&H->mbar, 1);
     fence_mbar_init();
     H->tables_loaded = -1;
+    H->job_loaded = -1;
   }
   __syncthreads();
   uint32_t phase = 0;
-  bool pending_store = false;
+#ifdef PP_PHASE_TIMING
+  if (tid == 0)
+    for (int k = 0; k < 10; ++k) H->ph_cycles[k] = 0;
+  long long ph_last = clock64();
+#endif
 
   for (;;) {
     // ------------------------------------------------------------ work item
     if (tid == 0) {
-      if (pending_store) bulk_wait_read_all();  // staging is reused below
       const unsigned long long item = atomicAdd(L.work_counter, 1ull);
       uint32_t j = 0;
       if (L.jobs != nullptr && item < L.total_tiles) {
@@ -251,13 +327,26 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
       }
       H->item = item;
       H->job = j;
+      H->nconv = 0;
     }
-    pending_store = false;
     __syncthreads();
     const unsigned long long item = H->item;
     if (item >= L.total_tiles) break;
-    const Job& J = L.jobs ? L.jobs[H->job] : L.job0;
-    const Col* cols = L.jobs ? (L.cols + J.col0) : L.cols0;
+    if (H->job_loaded != static_cast<int32_t>(H->job)) {
+      const Job& src = L.jobs ? L.jobs[H->job] : L.job0;
+      const Col* csrc = L.jobs ? (L.cols + src.col0) : L.cols0;
+      const uint32_t* s32 = reinterpret_cast<const uint32_t*>(&src);
+      uint32_t* d32 = reinterpret_cast<uint32_t*>(&H->jd);
+      for (int i = tid; i < static_cast<int>(sizeof(Job) / 4); i += NT) d32[i] = s32[i];
+      const uint32_t ncol = (L.jobs ? L.tables[src.tables] : L.tables0).num_columns;
+      const uint64_t* c64 = reinterpret_cast<const uint64_t*>(csrc);
+      uint64_t* e64 = reinterpret_cast<uint64_t*>(H->cd);
+      for (uint32_t i = tid; i < ncol * (sizeof(Col) / 8); i += NT) e64[i] = c64[i];
+      __syncthreads();
+      if (tid == 0) H->job_loaded = static_cast<int32_t>(H->job);
+    }
+    const Job& J = H->jd;
+    const Col* cols = H->cd;
     const uint64_t deadline = globaltimer_ns() + L.timeout_ns;
 
     if (H->tables_loaded != static_cast<int32_t>(J.tables)) {
@@ -276,6 +365,7 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
       if (tid == 0) H->tables_loaded = static_cast<int32_t>(J.tables);
       __syncthreads();
     }
+    PP_PHASE(0);
 
     // ------------------------------------------------------- load the tile
     const uint64_t t = item - J.tile_base;
@@ -312,6 +402,7 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
       phase ^= 1u;
     }
     __syncthreads();
+    PP_PHASE(1);
 
     // valid bytes of this thread's chunk, chunk-relative [lo, hi)
     const int64_t cv0 = static_cast<int64_t>(v0) + static_cast<int64_t>(tid) * B;
@@ -337,24 +428,19 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
         const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
+          // zero-byte test of the word against every symbol; a flagged byte
+          // that is not a symbol (borrow from a zero byte below) is harmless:
+          // it is simulated on its own with the catch-all transition
           uint32_t acc = 0;
 #pragma unroll
           for (int s = 0; s < NSPEC; ++s) {
             const uint32_t x = wd[k] ^ rep[s];
-            acc |= (x - 0x01010101u) & ~x;  // some byte of x is zero
+            acc |= (x - 0x01010101u) & ~x;
           }
-          if (acc & 0x80808080u) {
-            uint32_t m = 0;
-#pragma unroll
-            for (int s = 0; s < NSPEC; ++s) {
-              const uint32_t x = wd[k] ^ rep[s];
-              m |= ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x);  // exactly the zero bytes
-            }
-            m &= 0x80808080u;
-            const uint32_t bits4 = (((m >> 7) * 0x00204081u) >> 21) & 0xFu;
-            const int pos = 16 * v + 4 * k;
-            spec[pos >> 6] |= static_cast<uint64_t>(bits4) << (pos & 63);
-          }
+          acc &= 0x80808080u;
+          const uint32_t bits4 = (((acc >> 7) * 0x00204081u) >> 21) & 0xFu;
+          const int pos = 16 * v + 4 * k;
+          spec[pos >> 6] |= static_cast<uint64_t>(bits4) << (pos & 63);
         }
       }
 #pragma unroll
@@ -365,17 +451,12 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
     uint64_t vec = kIdentityVec;
     {
       int prev = -1;
-#pragma unroll
-      for (int w = 0; w < MW; ++w) {
-        uint64_t m = spec[w];
-        while (m) {
-          const int p = 64 * w + __ffsll(static_cast<long long>(m)) - 1;
-          m &= m - 1;
-          const bool run = max(prev + 1, lo) < p;
-          const uint32_t g = TB.group_of[chunk[p]];
-          vec = vcompose(vec, run ? TB.trans_run[g] : TB.trans[g]);
-          prev = p;
-        }
+      BitIter<MW> it(spec);
+      for (int p = it.next(); p >= 0; p = it.next()) {
+        const bool run = max(prev + 1, lo) < p;
+        const uint32_t g = TB.group_of[chunk[p]];
+        vec = vcompose(vec, run ? TB.trans_run[g] : TB.trans[g]);
+        prev = p;
       }
       if (max(prev + 1, lo) < hi) vec = vcompose(vec, TB.trans[TB.catch_all]);
     }
@@ -385,12 +466,14 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
     const uint64_t vex = block_exclusive_scan<NT>(
         vec, [](uint64_t a, uint64_t b) { return vcompose(a, b); }, kIdentityVec, H->wsum64,
         &tile_vec);
+    PP_PHASE(2);
     if (warp == 0) {
       const uint64_t pre =
           lookback_word<StatePolicy>(J.st_state, t, tile_vec, kIdentityVec, deadline, J.misc);
       if (lane == 0) H->prefix_vec = pre;
     }
     __syncthreads();
+    PP_PHASE(3);
     const uint32_t tile_s0 = vget(H->prefix_vec, TB.start_state);
     const uint32_t tile_send = vget(tile_vec, tile_s0);
     const uint32_t s_start = vget(vex, tile_s0);
@@ -398,7 +481,10 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
     // ------------------------------------------- a4: re-simulation, tags
     uint64_t dm[MW], fm[MW], rm[MW];
 #pragma unroll
-    for (int w = 0; w < MW; ++w) dm[w] = fm[w] = rm[w] = 0;
+    for (int w = 0; w < MW; ++w) {
+      dm[w] = bit_range(lo - 64 * w, hi - 64 * w) & ~spec[w];  // runs are data unless fixed below
+      fm[w] = rm[w] = 0;
+    }
     uint32_t s_end;
     {
       const uint32_t inv = TB.invalid_state;
@@ -411,35 +497,36 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
         const uint32_t s1 = vget(t_ca, s);
         const uint32_t tag0 = (e_ca >> (2 * s)) & 3u, tagr = (e_ca >> (2 * s1)) & 3u;
         if (s != inv && s1 == inv && inv_pos < 0) inv_pos = rs;
+        if ((tag0 | tagr) != PP_TAG_DATA) {  // rare: a run that is not all data
 #pragma unroll
-        for (int w = 0; w < MW; ++w) {
-          const uint64_t b0 = bit_range(rs - 64 * w, rs + 1 - 64 * w);
-          const uint64_t br = bit_range(rs + 1 - 64 * w, re - 64 * w);
-          dm[w] |= (tag0 == PP_TAG_DATA ? b0 : 0) | (tagr == PP_TAG_DATA ? br : 0);
-          fm[w] |= (tag0 == PP_TAG_FIELD ? b0 : 0) | (tagr == PP_TAG_FIELD ? br : 0);
-          rm[w] |= (tag0 == PP_TAG_RECORD ? b0 : 0) | (tagr == PP_TAG_RECORD ? br : 0);
+          for (int w = 0; w < MW; ++w) {
+            const uint64_t b0 = bit_range(rs - 64 * w, rs + 1 - 64 * w);
+            const uint64_t br = bit_range(rs + 1 - 64 * w, re - 64 * w);
+            dm[w] &= ~((tag0 != PP_TAG_DATA ? b0 : 0) | (tagr != PP_TAG_DATA ? br : 0));
+            fm[w] |= (tag0 == PP_TAG_FIELD ? b0 : 0) | (tagr == PP_TAG_FIELD ? br : 0);
+            rm[w] |= (tag0 == PP_TAG_RECORD ? b0 : 0) | (tagr == PP_TAG_RECORD ? br : 0);
+          }
         }
         s = s1;
       };
+      BitIter<MW> it(spec);
+      for (int p = it.next(); p >= 0; p = it.next()) {
+        const int rs = max(prev + 1, lo);
+        if (rs < p) run(rs, p);
+        const uint32_t g = TB.group_of[chunk[p]];
+        const uint32_t tag = (TB.emit[g] >> (2 * s)) & 3u;
+        const uint32_t ns = vget(TB.trans[g], s);
+        if (s != inv && ns == inv && inv_pos < 0) inv_pos = p;
+        // a special symbol is never data unless its tag says so
 #pragma unroll
-      for (int w = 0; w < MW; ++w) {
-        uint64_t m = spec[w];
-        while (m) {
-          const int p = 64 * w + __ffsll(static_cast<long long>(m)) - 1;
-          m &= m - 1;
-          const int rs = max(prev + 1, lo);
-          if (rs < p) run(rs, p);
-          const uint32_t g = TB.group_of[chunk[p]];
-          const uint32_t tag = (TB.emit[g] >> (2 * s)) & 3u;
-          const uint32_t ns = vget(TB.trans[g], s);
-          if (s != inv && ns == inv && inv_pos < 0) inv_pos = p;
-          const uint64_t bit = 1ull << (p & 63);
+        for (int w = 0; w < MW; ++w) {
+          const uint64_t bit = (p >> 6) == w ? (1ull << (p & 63)) : 0ull;
           if (tag == PP_TAG_DATA) dm[w] |= bit;
           else if (tag == PP_TAG_FIELD) fm[w] |= bit;
           else if (tag == PP_TAG_RECORD) rm[w] |= bit;
-          s = ns;
-          prev = p;
         }
+        s = ns;
+        prev = p;
       }
       {
         const int rs = max(prev + 1, lo);
@@ -471,12 +558,14 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
     uint32_t rc_tile;
     const uint32_t rc_ex = block_exclusive_scan<NT>(rc_pack(nrec, ncol, nrec > 0), rc_combine,
                                                     rc_pack(0, 0, false), H->wsum32, &rc_tile);
+    PP_PHASE(4);
     if (warp == 0) {
       const uint64_t agg = tc_pack(rc_tile & 0xFFFFu, (rc_tile >> 16) & kColSat, (rc_tile >> 31) != 0);
       const uint64_t pre = lookback_word<RcPolicy>(J.st_rc, t, agg, tc_pack(0, 0, true), deadline, J.misc);
       if (lane == 0) H->prefix_rc = pre;
     }
     __syncthreads();
+    PP_PHASE(5);
     const uint64_t tile_row0 = H->prefix_rc & kRecMask;
     const uint32_t tile_col0 = static_cast<uint32_t>((H->prefix_rc >> 40) & 0x1FFFFF);
     const uint64_t row_start = tile_row0 + (rc_ex & 0xFFFFu);
@@ -490,18 +579,18 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
       for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
       uint32_t c = col_start;
       int pos = lo;
+      uint64_t dl[MW];
 #pragma unroll
-      for (int w = 0; w < MW; ++w) {
-        uint64_t dl = fm[w] | rm[w];
-        while (dl) {
-          const int d = 64 * w + __ffsll(static_cast<long long>(dl)) - 1;
-          dl &= dl - 1;
-          if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += popc_range(dm, pos, d);
-          c = ((rm[w] >> (d & 63)) & 1ull) ? 0u : min(c + 1, kColSat);
-          pos = d + 1;
-        }
+      for (int w = 0; w < MW; ++w) dl[w] = fm[w] | rm[w];
+      BitIter<MW> it(dl);
+      for (;;) {
+        const int d = it.next();
+        const int e = d >= 0 ? d : hi;
+        if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += popc_range(dm, pos, e);
+        if (d < 0) break;
+        c = test_bit(rm, d) ? 0u : min(c + 1, kColSat);
+        pos = d + 1;
       }
-      if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += popc_range(dm, pos, hi);
 
       // block scan of the per-slot counts, two 16-bit slots per word
       const uint32_t K = (NS + 1) / 2;
@@ -538,63 +627,54 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
         }
       }
       __syncthreads();
+      PP_PHASE(6);
 
-      // chain 3: per-slot byte counts, summed over the predecessors
+      // chain 3: per-slot byte counts, summed over the predecessors.  Each
+      // slot is its own single-word scan: flag | 48-bit count.
       if (warp == 0) {
-        int64_t* agg = J.st_bytes_agg + t * NS;
-        int64_t* inc = J.st_bytes_inc + t * NS;
-        int64_t acc[PP_MAX_STRING_COLUMNS];
-#pragma unroll
-        for (int k = 0; k < PP_MAX_STRING_COLUMNS; ++k) acc[k] = 0;
+        uint64_t* st3 = J.st_bytes + t * NS;
+        int64_t myacc = 0;  // lane k accumulates slot k
         if (t > 0) {
-          if (lane < static_cast<int>(NS)) st_relaxed_s64(&agg[lane], H->tile_tot[lane]);
-          __syncwarp();
-          __threadfence();
-          if (lane == 0) st_release_u32(&J.st_bytes_flag[t], 1u);
+          if (lane < static_cast<int>(NS)) st_relaxed_u64(&st3[lane], kFlagAgg | H->tile_tot[lane]);
           int64_t idx = static_cast<int64_t>(t) - 1;
-          for (;;) {
+          uint32_t pending = (1u << NS) - 1u;  // slots without an inclusive prefix yet
+          while (pending) {
             const int64_t mine = idx - lane;
-            uint32_t f = 2u;
-            if (mine >= 0) {
-              f = ld_acquire_u32(&J.st_bytes_flag[mine]);
-              while (f == 0u) {
-                if (globaltimer_ns() > deadline) {
-                  atomicOr(&J.misc->timeout, 1u);
-                  f = 3u;
+#pragma unroll 1
+            for (uint32_t k = 0; k < NS; ++k) {
+              if (!((pending >> k) & 1u)) continue;
+              uint64_t w = kFlagInc;  // before tile 0
+              if (mine >= 0) w = ld_relaxed_u64(&J.st_bytes[mine * NS + k]);
+              bool done = false;
+              int take;
+              for (;;) {
+                take = window_take(__ballot_sync(0xffffffffu, (w & kFlagMask) != 0),
+                                   __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagInc), &done);
+                if (take > 0) break;
+                const bool expired = __shfl_sync(0xffffffffu, globaltimer_ns() > deadline ? 1 : 0, 0) != 0;
+                if (expired) {
+                  if (lane == 0) atomicOr(&J.misc->timeout, 1u);
+                  done = true;
+                  take = 0;
                   break;
                 }
-                __nanosleep(32);
-                f = ld_acquire_u32(&J.st_bytes_flag[mine]);
+                __nanosleep(20);
+                if ((w & kFlagMask) == 0) w = ld_relaxed_u64(&J.st_bytes[mine * NS + k]);
               }
-            }
-            const uint32_t incmask = __ballot_sync(0xffffffffu, f >= 2u);
-            const int firstinc = incmask ? __ffs(incmask) - 1 : 32;
-            const bool use = mine >= 0 && lane <= firstinc && f != 3u;
-            const int64_t* src = (f == 2u ? J.st_bytes_inc : J.st_bytes_agg) + (mine >= 0 ? mine : 0) * NS;
+              long long x = lane < take ? static_cast<long long>(w & ~kFlagMask) : 0ll;
 #pragma unroll
-            for (int k = 0; k < PP_MAX_STRING_COLUMNS; ++k) {
-              if (k < static_cast<int>(NS)) {
-                long long x = use ? ld_relaxed_s64(&src[k]) : 0ll;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-                acc[k] += x;
-              }
+              for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+              if (lane == static_cast<int>(k)) myacc += x;
+              if (done) pending &= ~(1u << k);
             }
-            if (incmask) break;
             idx -= 32;
           }
         }
         if (lane < static_cast<int>(NS)) {
-          int64_t mine_acc = 0;
-#pragma unroll
-          for (int k = 0; k < PP_MAX_STRING_COLUMNS; ++k)
-            if (k == lane) mine_acc = acc[k];
-          H->col_base[lane] = mine_acc;
-          st_relaxed_s64(&inc[lane], mine_acc + H->tile_tot[lane]);
+          H->col_base[lane] = myacc;
+          st_relaxed_u64(&st3[lane], kFlagInc | static_cast<uint64_t>(myacc + H->tile_tot[lane]));
         }
         __syncwarp();
-        __threadfence();
-        if (lane == 0) st_release_u32(&J.st_bytes_flag[t], 2u);
         if (lane == 0) {
           // staging regions share the destination's 16-byte phase so that
           // their aligned interiors can be bulk-stored
@@ -608,6 +688,7 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
         }
       }
       __syncthreads();
+      PP_PHASE(7);
     }
 
     // ----------------- a6 / a7 / a8: gather, offsets, conversion, rejects
@@ -624,48 +705,69 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
           store_value(cols[c2], TB.col_type[c2], r, 0);
       }
     };
-    // Converts the numeric field (r, c) that starts at chunk position q.
-    auto convert_at = [&](uint64_t r, uint32_t c, int q) {
+    // Converts the numeric field (r, c) that starts at tile position p0.  The
+    // common case -- the field ends inside the tile and its data bytes are
+    // contiguous -- parses straight from shared memory; otherwise the data
+    // bytes are gathered first (through the tile's masks, then from global
+    // memory past the tile, re-simulating from the tile's end state).
+    auto convert_at = [&](uint64_t r, uint32_t c, int p0) {
       const uint32_t type = TB.col_type[c];
-      uint8_t buf[kNumericMaxLen + 1];
-      int n = 0;
-      bool ended = false;
-      int p = tid * B + q;
       const int tend = static_cast<int>(v1 - v0);
-      while (p < tend && !ended && n <= kNumericMaxLen) {
-        const int u = p / B, i = p - u * B;
-        const int span = min(min(64 - (i & 63), B - i), tend - p);
+      int first = -1, last = -1, n = 0;
+      bool ended = false;
+      int x = p0;
+      while (x < tend) {
+        const int u = x / B, i = x - u * B;
+        const int span = min(min(64 - (i & 63), B - i), tend - x);
         const uint64_t dlw = s_dl[u * MW + (i >> 6)] >> (i & 63);
         const uint64_t dmw = s_dm[u * MW + (i >> 6)] >> (i & 63);
         const int dpos = dlw ? __ffsll(static_cast<long long>(dlw)) - 1 : 64;
-        const int stop = min(dpos, span);
-        uint64_t bits = dmw & bits_below(stop);
-        while (bits && n <= kNumericMaxLen) {
-          const int j = __ffsll(static_cast<long long>(bits)) - 1;
-          bits &= bits - 1;
-          buf[n++] = s_tile[p + j];
+        const uint64_t bits = dmw & bits_below(min(dpos, span));
+        if (bits) {
+          if (first < 0) first = x + __ffsll(static_cast<long long>(bits)) - 1;
+          last = x + 63 - __clzll(static_cast<long long>(bits));
+          n += __popcll(bits);
         }
-        if (dpos < span) ended = true;
-        p += span;
-      }
-      if (!ended && n <= kNumericMaxLen && p >= tend && v1 < VL) {
-        uint32_t s = tile_send;
-        for (uint64_t x = v1; x < VL; ++x) {
-          const uint8_t b = vbase[x];
-          const uint32_t g = TB.group_of[b];
-          const uint32_t tag = (TB.emit[g] >> (2 * s)) & 3u;
-          s = vget(TB.trans[g], s);
-          if (tag == PP_TAG_DATA) {
-            buf[n++] = b;
-            if (n > kNumericMaxLen) break;
-          } else if (tag != PP_TAG_CONTROL) {
-            break;
-          }
-          if (s == TB.invalid_state) break;
+        if (dpos < span) {
+          ended = true;
+          break;
         }
+        x += span;
+        if (n > kNumericMaxLen) break;
       }
+      if (!ended && x >= tend && v1 >= VL) ended = true;  // the input ends the field
       uint64_t val = 0;
-      const int st = n > kNumericMaxLen ? kConvFail : convert_value(type, buf, n, &val);
+      int st;
+      if (n > kNumericMaxLen) {
+        st = kConvFail;
+      } else if (ended && (n == 0 || last - first + 1 == n)) {
+        st = convert_value(type, s_tile + (n ? first : 0), n, &val);
+      } else {
+        uint8_t buf[kNumericMaxLen + 1];
+        int m = 0;
+        for (int y = p0; y < tend && m <= kNumericMaxLen; ++y) {
+          const int u = y / B, i = y - u * B;
+          if ((s_dl[u * MW + (i >> 6)] >> (i & 63)) & 1ull) break;
+          if ((s_dm[u * MW + (i >> 6)] >> (i & 63)) & 1ull) buf[m++] = s_tile[y];
+        }
+        if (!ended && m <= kNumericMaxLen) {
+          uint32_t s = tile_send;
+          for (uint64_t g = v1; g < VL; ++g) {
+            const uint8_t b = vbase[g];
+            const uint32_t grp = TB.group_of[b];
+            const uint32_t tag = (TB.emit[grp] >> (2 * s)) & 3u;
+            s = vget(TB.trans[grp], s);
+            if (tag == PP_TAG_DATA) {
+              buf[m++] = b;
+              if (m > kNumericMaxLen) break;
+            } else if (tag != PP_TAG_CONTROL) {
+              break;
+            }
+            if (s == TB.invalid_state) break;
+          }
+        }
+        st = m > kNumericMaxLen ? kConvFail : convert_value(type, buf, m, &val);
+      }
       store_value(cols[c], type, r, val);
       if (st != kConvOk) {
         const uint32_t bit = 1u << (r & 31);
@@ -687,89 +789,111 @@ __global__ void __launch_bounds__(Shape::NT) pp_tile_kernel(const __grid_constan
     };
 
     {
+      // Walk the chunk's delimiters once.  Each event ends the current field
+      // piece (its string bytes are staged), a delimiter also ends the field
+      // (offset, record end) and opens the next one (converted here if
+      // numeric).  The end of the input closes the trailing record.
       uint32_t c = col_start;
       uint64_t r = row_start;
       int pos = lo;
-      // the input's first field has no delimiter before it
-      if (t == 0 && tid == 0 && J.len > 0 && C > 0 && TB.num_slot[0] != 0xFF && rows_cap > 0)
-        convert_at(0, 0, lo);
+      const bool eof_here = last_tile && lo < hi && cv0 + hi == static_cast<int64_t>(VL);
+      bool trailing = eof_here && !test_bit(rm, hi - 1) && ((TB.accept_mask >> s_end) & 1u);
+      bool opens = t == 0 && tid == 0 && J.len > 0;  // the input's first field
+      uint64_t dl[MW];
 #pragma unroll
-      for (int w = 0; w < MW; ++w) {
-        uint64_t dl = fm[w] | rm[w];
-        while (dl) {
-          const int d = 64 * w + __ffsll(static_cast<long long>(dl)) - 1;
-          dl &= dl - 1;
-          const uint32_t slot = c < C ? TB.str_slot[c] : 0xFFu;
-          if (slot != 0xFF) {
-            stage_piece(slot, pos, d);
-            if (r < rows_cap) cols[c].offsets[r + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
-          }
-          const bool is_rd = (rm[w] >> (d & 63)) & 1ull;
-          if (is_rd) {
-            record_end(r, c + 1 > kColSat ? kColSat : c + 1);
-            ++r;
-            c = 0;
+      for (int w = 0; w < MW; ++w) dl[w] = fm[w] | rm[w];
+      BitIter<MW> it(dl);
+      for (;;) {
+        if (opens && c < C && TB.num_slot[c] != 0xFF && r < rows_cap) {
+          const uint32_t slot_i = atomicAdd(&H->nconv, 1u);
+          if (slot_i < static_cast<uint32_t>(Shape::kConvCap)) {
+            s_conv_a[slot_i] = static_cast<uint32_t>(tid * B + pos) | (c << 16);
+            s_conv_b[slot_i] = static_cast<uint16_t>(r - tile_row0);
           } else {
-            c = min(c + 1, kColSat);
+            convert_at(r, c, tid * B + pos);
           }
-          const bool at_end = (cv0 + d + 1) >= static_cast<int64_t>(VL);
-          if (c < C && TB.num_slot[c] != 0xFF && r < rows_cap && !(is_rd && at_end))
-            convert_at(r, c, d + 1);
-          pos = d + 1;
         }
-      }
-      if (c < C && TB.str_slot[c] != 0xFF) stage_piece(TB.str_slot[c], pos, hi);
-
-      // end of input: the trailing record, and the totals
-      if (last_tile && lo < hi && cv0 + hi == static_cast<int64_t>(VL)) {
-        const bool last_rd = test_bit(rm, hi - 1);
-        const bool accept = (TB.accept_mask >> s_end) & 1u;
-        uint64_t rows = r;
-        if (!last_rd && accept) {
-          const uint32_t slot = c < C ? TB.str_slot[c] : 0xFFu;
-          if (slot != 0xFF && r < rows_cap)
-            cols[c].offsets[r + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
+        const int d = it.next();
+        int e;
+        bool is_rd = false, ends_field = true;
+        if (d >= 0) {
+          e = d;
+          is_rd = test_bit(rm, d);
+        } else if (trailing) {
+          e = hi;
+          is_rd = true;
+          trailing = false;
+        } else {
+          e = hi;
+          ends_field = false;
+        }
+        const uint32_t slot = c < C ? TB.str_slot[c] : 0xFFu;
+        if (slot != 0xFF) {
+          stage_piece(slot, pos, e);
+          if (ends_field && r < rows_cap) cols[c].offsets[r + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
+        }
+        if (!ends_field) break;
+        if (is_rd) {
           record_end(r, c + 1 > kColSat ? kColSat : c + 1);
-          rows = r + 1;
+          ++r;
+          c = 0;
+        } else {
+          c = min(c + 1, kColSat);
         }
-        J.misc->rows = static_cast<int64_t>(rows);
+        pos = e + 1;
+        opens = d >= 0 && !(is_rd && (cv0 + e + 1) >= static_cast<int64_t>(VL));
+        if (d < 0) break;
+      }
+      if (eof_here) {
+        J.misc->rows = static_cast<int64_t>(r);  // read by the finalize kernel only
         J.misc->final_state = static_cast<int32_t>(s_end);
         for (uint32_t k = 0; k < NS; ++k) J.misc->bytes_total[k] = H->col_base[k] + H->tile_tot[k];
-        __threadfence();
         J.misc->done = 1u;
       }
     }
 
-    // ----------------------------- write the gathered string bytes (TMA)
+    // --------------------- a7: queued numeric fields, one per thread
+    __syncthreads();
+    {
+      const uint32_t nq = min(H->nconv, static_cast<uint32_t>(Shape::kConvCap));
+      for (uint32_t i = tid; i < nq; i += NT) {
+        const uint32_t a = s_conv_a[i];
+        convert_at(tile_row0 + s_conv_b[i], a >> 16, static_cast<int>(a & 0xFFFFu));
+      }
+    }
+
+    // ------------------- write the gathered string bytes, 16 B per thread
     if (NS > 0) {
-      fence_proxy_async_smem();
       __syncthreads();
+      PP_PHASE(8);
       for (uint32_t k = 0; k < NS; ++k) {
         const Col& col = cols[H->str_col[k]];
-        const uint64_t cap = col.values_cap;
         const uint64_t c0 = static_cast<uint64_t>(H->col_base[k]);
-        const uint64_t c1 = min(c0 + H->tile_tot[k], cap);
+        const uint64_t c1 = min(c0 + H->tile_tot[k], col.values_cap);
         if (c1 <= c0) continue;
         uint8_t* gbase = static_cast<uint8_t*>(col.values);
         const uintptr_t g0 = reinterpret_cast<uintptr_t>(gbase + c0);
         const uintptr_t g1 = reinterpret_cast<uintptr_t>(gbase + c1);
         const uintptr_t A = (g0 + 15) & ~uintptr_t(15), Bn = g1 & ~uintptr_t(15);
-        const uint8_t* sbase = s_stage + H->stage_off[k];
-        if (tid == 0 && Bn > A) {
-          tma_store_1d(reinterpret_cast<void*>(A), sbase + (A - g0), static_cast<uint32_t>(Bn - A));
-          pending_store = true;
-        }
+        const uint8_t* sbase = s_stage + H->stage_off[k];  // same 16-byte phase as g0
+        const int nvec = Bn > A ? static_cast<int>((Bn - A) >> 4) : 0;
+        const uint4* sv = reinterpret_cast<const uint4*>(sbase + (A - g0));
+        uint4* gv = reinterpret_cast<uint4*>(A);
+        for (int i = tid; i < nvec; i += NT) gv[i] = sv[i];
         if (tid < 32) {
-          const uintptr_t x = tid < 16 ? g0 + tid : max(Bn, A) + (tid - 16);
-          const bool ok = tid < 16 ? (x < A && x < g1) : (x < g1);
-          if (ok) *reinterpret_cast<uint8_t*>(x) = sbase[x - g0];
+          const uintptr_t y = tid < 16 ? g0 + tid : max(Bn, A) + (tid - 16);
+          const bool ok = tid < 16 ? (y < A && y < g1) : (y < g1);
+          if (ok) *reinterpret_cast<uint8_t*>(y) = sbase[y - g0];
         }
       }
-      if (tid == 0 && pending_store) bulk_commit();
     }
     __syncthreads();
+    PP_PHASE(9);
   }
-  if (tid == 0) bulk_wait_all();
+#ifdef PP_PHASE_TIMING
+  if (tid == 0 && L.phase_cycles != nullptr)
+    for (int k = 0; k < 10; ++k) atomicAdd(&L.phase_cycles[k], static_cast<unsigned long long>(H->ph_cycles[k]));
+#endif
 }
 
 }  // namespace pp

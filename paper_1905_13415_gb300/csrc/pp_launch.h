@@ -17,5 +17,8 @@ ShapeInfo shape_info_tiny();    // 32 threads x 16 B   =   512 B tiles
 ShapeInfo shape_info_small();   // 64 threads x 48 B   =  3 KiB tiles
 ShapeInfo shape_info_mid();     // 256 threads x 112 B = 28 KiB tiles
 ShapeInfo shape_info_wide();    // 128 threads x 208 B = 26 KiB tiles
+ShapeInfo shape_info_m128();    // 128 threads x 112 B = 14 KiB tiles, 4 blocks / SM
+ShapeInfo shape_info_m128x6();  // 128 threads x 112 B = 14 KiB tiles, 6 blocks / SM
+ShapeInfo shape_info_s128();    // 128 threads x 48 B  =  6 KiB tiles, 8 blocks / SM
 
 }  // namespace pp

@@ -6,9 +6,9 @@
 #include "pp_kernel.cuh"
 #include "pp_launch.h"
 
-#define PP_DEFINE_SHAPE(NAME, NT_, VPT_)                                                         \
+#define PP_DEFINE_SHAPE(NAME, NT_, VPT_, MINB_)                                                         \
   namespace pp {                                                                                 \
-  using Shape_##NAME = TileShape<NT_, VPT_>;                                                     \
+  using Shape_##NAME = TileShape<NT_, VPT_, MINB_>;                                                     \
   static const void* kernel_ptr_##NAME(int nspec) {                                              \
     if (nspec <= 4) return reinterpret_cast<const void*>(&pp_tile_kernel<Shape_##NAME, 4>);      \
     if (nspec <= 8) return reinterpret_cast<const void*>(&pp_tile_kernel<Shape_##NAME, 8>);      \

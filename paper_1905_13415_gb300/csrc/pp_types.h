@@ -56,9 +56,7 @@ struct Job {
   // scratch
   uint64_t* st_state;   // chain 1: per tile, flag | packed vector
   uint64_t* st_rc;      // chain 2: per tile, flag | records, column offset
-  uint32_t* st_bytes_flag;  // chain 3: per tile flag
-  int64_t* st_bytes_agg;    // chain 3: per tile per string slot
-  int64_t* st_bytes_inc;
+  uint64_t* st_bytes;   // chain 3: per tile, per string slot, flag | byte count
   uint32_t* fail_bits;  // per row: rejected
   uint32_t* null_bits;  // per numeric slot, per row: empty or unconvertible
   Misc* misc;
@@ -75,10 +73,14 @@ struct Launch {
   uint64_t total_tiles;
   unsigned long long* work_counter;
   uint64_t timeout_ns;
+  unsigned long long* phase_cycles;  // profiling builds only; else nullptr
   Job job0;
   Tables tables0;
   Col cols0[PP_MAX_COLUMNS];
 };
+
+static_assert(sizeof(Job) % 8 == 0 && sizeof(Tables) % 4 == 0 && sizeof(Col) % 8 == 0,
+              "descriptors are copied in 4- and 8-byte words");
 
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagInc = 2ull << 62;
