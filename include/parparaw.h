@@ -227,6 +227,33 @@ typedef struct pp_batch_item {
  * item's parser. */
 pp_status parparaw_parse_batch(const pp_batch_item* items, uint64_t n, void* stream);
 
+/* Size of the fixed device scratch behind parparaw_parse_noalloc. */
+#define PP_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* parparaw_parse without any allocation (the paper has no counterpart; it is
+ * an interface convenience).  Some callers cannot allocate device memory on
+ * the call path: services that reserve all device memory up front and forbid
+ * the CUDA allocator afterwards, callers that account every byte through
+ * their own allocator, or latency-bound paths where an allocation may stall
+ * other work on the device.  This entry point takes its scratch (tile status
+ * words, reject / null bitmaps, counters) from one fixed array of
+ * PP_NOALLOC_SCRATCH_BYTES in device memory that the library defines; every
+ * GPU that loads the library holds that array until the process exits.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - Arguments, output layout and results are those of parparaw_parse.
+ *   - Returns PP_E_UNSUPPORTED, before launching anything, when the scratch
+ *     this parse needs (it grows with len / tile size, with rows_cap and with
+ *     the number of numeric columns) exceeds PP_NOALLOC_SCRATCH_BYTES.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and it keeps the previous
+ *     call's contents; each call clears what must start at zero itself.
+ *     Calls whose work overlaps on the GPU (other streams, other threads)
+ *     race on the array: order them, e.g. on one stream. */
+pp_status parparaw_parse_noalloc(const pp_parser* parser, const uint8_t* input, uint64_t len,
+                                 const pp_columns* out, void* stream);
+
 /* Records the two CUDA events (cudaEvent_t passed as void*) on the stream
  * immediately before and after the main parse kernel of every later parse or
  * batch made with this parser, so that a caller can time that kernel alone.

@@ -22,7 +22,9 @@ OPT_TILE_CONFIG, OPT_TIMEOUT_MS, OPT_GRID_LIMIT = 1, 2, 3
 
 EXPORTED = ["parparaw_create", "parparaw_destroy", "parparaw_set_option", "parparaw_get_info",
             "parparaw_parse", "parparaw_parse_batch", "parparaw_set_kernel_events",
-            "parparaw_status_string"]
+            "parparaw_status_string", "parparaw_parse_noalloc"]
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class pp_dfa(ctypes.Structure):
@@ -102,6 +104,8 @@ def load():
     L.parparaw_get_info.restype = ctypes.c_int
     L.parparaw_parse.argtypes = [vp, vp, ctypes.c_uint64, ctypes.POINTER(pp_columns), vp]
     L.parparaw_parse.restype = ctypes.c_int
+    L.parparaw_parse_noalloc.argtypes = [vp, vp, ctypes.c_uint64, ctypes.POINTER(pp_columns), vp]
+    L.parparaw_parse_noalloc.restype = ctypes.c_int
     L.parparaw_parse_batch.argtypes = [ctypes.POINTER(pp_batch_item), ctypes.c_uint64, vp]
     L.parparaw_parse_batch.restype = ctypes.c_int
     L.parparaw_set_kernel_events.argtypes = [vp, vp, vp]

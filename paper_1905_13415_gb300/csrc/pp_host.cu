@@ -638,3 +638,109 @@ extern "C" pp_status parparaw_parse_batch(const pp_batch_item* items, uint64_t n
   delete Lp;
   return st;
 }
+
+// ================================================= allocation-free parse ===
+//
+// parparaw_parse_noalloc: the same init / tile / finalize kernels as
+// parparaw_parse, with the scratch taken from a fixed array in device memory
+// instead of a stream-ordered allocation.  See include/parparaw.h.
+
+namespace pp {
+namespace {
+
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[PP_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint8_t* g_noalloc_dev_ptr[kNoallocMaxDevices] = {};
+
+// The array's name is only a host-side handle; kernels need its device
+// address, looked up once per device with that device current.
+cudaError_t noalloc_scratch_ptr(int dev, uint8_t** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_dev_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_dev_ptr[dev] = static_cast<uint8_t*>(p);
+  }
+  *out = g_noalloc_dev_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace pp
+
+extern "C" pp_status parparaw_parse_noalloc(const pp_parser* P, const uint8_t* input, uint64_t len,
+                                            const pp_columns* out, void* stream_) {
+  if (P == nullptr || (input == nullptr && len > 0)) return PP_E_ARG;
+  pp_status st = check_columns(P, out);
+  if (st != PP_OK) return st;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return map_err(e);
+  if (dev < 0 || dev >= kNoallocMaxDevices) return PP_E_UNSUPPORTED;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const ShapeInfo shape = shape_for(P->tile_config);
+
+  Launch L;  // on the stack: no host allocation either
+  std::memset(&L, 0, sizeof(L));
+  Job& J = L.job0;
+  J.input = input;
+  J.len = len;
+  J.head = len > 0 ? (reinterpret_cast<uintptr_t>(input) & 15u) : 0;
+  J.ntiles = len > 0 ? (J.head + len + shape.tile_bytes - 1) / shape.tile_bytes : 0;
+  J.rows_cap = out->rows_cap;
+  J.bit_words = (out->rows_cap + 31) / 32 + 1;
+  J.row_valid = out->row_valid;
+  J.result = out->result;
+  const ScratchPlan plan = plan_scratch(64, J.ntiles, P->tab.num_str, P->tab.num_num, J.bit_words);
+  if (plan.total > PP_NOALLOC_SCRATCH_BYTES) return PP_E_UNSUPPORTED;  // input or rows_cap too large
+  uint8_t* scratch = nullptr;
+  if ((e = noalloc_scratch_ptr(dev, &scratch)) != cudaSuccess) return map_err(e);
+  L.tables0 = P->tab;
+  for (uint32_t c = 0; c < out->num_columns; ++c) {
+    L.cols0[c].values = out->cols[c].values;
+    L.cols0[c].offsets = out->cols[c].offsets;
+    L.cols0[c].validity = out->cols[c].validity;
+    L.cols0[c].values_cap = out->cols[c].values_cap;
+  }
+  fill_job(J, plan, scratch);
+  L.njobs = 1;
+  L.total_tiles = J.ntiles;
+  L.work_counter = reinterpret_cast<unsigned long long*>(scratch);
+  L.timeout_ns = P->timeout_ns;
+
+  // init clears everything the tile kernel needs at zero (status words,
+  // bitmaps, counters), since the array keeps the previous call's contents
+  const uint32_t gx_init = static_cast<uint32_t>(std::max<uint64_t>(
+      1, std::min<uint64_t>((std::max(J.ntiles * std::max<uint32_t>(1, P->tab.num_str), J.bit_words * 16) +
+                             kBlockInit - 1) / kBlockInit, 1024)));
+  pp_init_kernel<<<dim3(gx_init, 1), kBlockInit, 0, stream>>>(L);
+  if ((e = cudaGetLastError()) != cudaSuccess) return map_err(e);
+  if (L.total_tiles > 0) {
+    const void* kern = shape.kernel(nspec_of(P->tab));
+    int sms = 0, per_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return map_err(e);
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(shape.smem_bytes))) != cudaSuccess)
+      return map_err(e);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, shape.threads, shape.smem_bytes)) !=
+        cudaSuccess)
+      return map_err(e);
+    uint64_t grid = std::min<uint64_t>(L.total_tiles, static_cast<uint64_t>(std::max(per_sm, 1)) * sms);
+    if (P->grid_limit > 0) grid = std::min<uint64_t>(grid, static_cast<uint64_t>(P->grid_limit));
+    if (P->ev_start) cudaEventRecord(P->ev_start, stream);
+    void* args[] = {&L};
+    if ((e = cudaLaunchKernel(kern, dim3(static_cast<uint32_t>(grid)), dim3(shape.threads), args, shape.smem_bytes,
+                              stream)) != cudaSuccess)
+      return map_err(e);
+    if (P->ev_stop) cudaEventRecord(P->ev_stop, stream);
+  }
+  const uint32_t gx_fin = static_cast<uint32_t>(
+      std::max<uint64_t>(1, std::min<uint64_t>((J.bit_words + kBlockFinal - 1) / kBlockFinal, 1024)));
+  pp_finalize_kernel<<<dim3(gx_fin, 1), kBlockFinal, 0, stream>>>(L);
+  if ((e = cudaGetLastError()) != cudaSuccess) return map_err(e);
+  return PP_OK;
+}
