@@ -171,6 +171,134 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args, dev, log):
+    """Config 4: 10,000 inputs (log-normal sizes 1 KB..64 MB, ~6e9 B, half CSV,
+    half web logs) in one persistent launch per step, tile shape autotuned."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1905_13415_gb300 import Batch, Parser, formats
+    from paper_1905_13415_gb300.autotune import autotune, time_batch
+
+    n = args.batch_inputs
+    sizes, kinds, seeds = synth.batch_plan(n, args.batch_bytes, synth.BASE_SEED + 4)
+    host = torch.empty(int(sizes.sum()), dtype=torch.uint8, pin_memory=True)
+    t0 = time.perf_counter()
+    offs, lens, rows = synth.generate_batch_into(kinds, seeds, sizes, host.data_ptr())
+    gen_s = time.perf_counter() - t0
+    data = host.to(dev)
+    parsers = {k: Parser(formats.by_name(synth.DIALECT[k]), synth.SCHEMAS[k]) for k in ("mixed", "log")}
+    items = []
+    for i in range(n):
+        p = parsers[kinds[i]]
+        d = data[int(offs[i]): int(offs[i]) + int(lens[i])]
+        out = p.allocate(max(int(rows[i]), 1), [max(int(lens[i]), 1)] * len(p.types), device=dev)
+        items.append((p, d, out))
+    total = int(lens.sum())
+    # autotune on a sample of the inputs
+    rng = np.random.default_rng(7)
+    sample = [items[i] for i in sorted(rng.choice(n, size=min(400, n), replace=False))]
+    best, tuned = autotune(sample, reps=3)
+    # one prepared batch, timed
+    stream = torch.cuda.current_stream()
+    b = Batch(items)
+    for _ in range(args.warmup):
+        b.launch(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(3, min(args.steps, 10))
+    e0.record(stream)
+    for _ in range(steps):
+        b.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / steps
+    b.close()
+    bad = 0
+    for i, (p, d, out) in enumerate(items):
+        res = out.result()
+        if res.status != 0 or res.rows != int(rows[i]):
+            bad += 1
+    # the plain per-input loop on the same inputs
+    for p, d, out in items[:50]:
+        p.parse_into(d, out, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for p, d, out in items:
+        p.parse_into(d, out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1)
+    # full parity against the oracle on a sample of inputs
+    from tests.parity import assert_same, oracle_parse
+    checked = 0
+    b = Batch(items)
+    b.launch(stream)
+    torch.cuda.synchronize()
+    b.close()
+    for i in sorted(rng.choice(n, size=min(12, n), replace=False)):
+        p, d, out = items[i]
+        raw = host[int(offs[i]): int(offs[i]) + int(lens[i])].numpy().tobytes()
+        res = out.result()
+        assert_same(out.to_host(res.rows), res, oracle_parse(synth.DIALECT[kinds[i]], synth.SCHEMAS[kinds[i]], raw))
+        checked += 1
+    del items, data
+    torch.cuda.empty_cache()
+    log(f"batched: {total} B in {batch_ms:.2f} ms, loop {loop_ms:.2f} ms, generator {gen_s:.1f} s")
+    return {"value": round(total / (batch_ms * 1e-3) / 1e9, 3), "unit": "GB/s", "inputs": n, "bytes": total,
+            "ms_per_step": round(batch_ms, 3), "steps": steps, "launches_per_step": 3,
+            "tile_config": best, "autotune_ms": {str(k): round(v, 3) for k, v in tuned.items()},
+            "plain_loop": {"value": round(total / (loop_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+                           "ms": round(loop_ms, 2), "launches": 3 * n},
+            "bad_results": bad, "oracle_checked_inputs": checked,
+            "workload": "10,000 inputs, log-normal sizes 1 KB..64 MB (~6e9 B), half RFC-4180 CSV, half web logs"}
+
+
+def run_served(args, dev, log):
+    """Config 5: Poisson arrivals at 2,000 req/s; request sizes log-normal
+    (median 64 KB, sigma 2) clipped to 4 KB..256 MB, payloads drawn from a
+    device-resident pool of mixed-CSV / review-CSV / web-log inputs; admission
+    capped by a 40 GB output arena; p50 / p99 latency vs the plain parse."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1905_13415_gb300 import Parser, formats
+    from paper_1905_13415_gb300.serve import Request, Server, run_trace, run_trace_plain
+
+    rng = np.random.default_rng(synth.BASE_SEED + 5)
+    npool = args.serve_pool
+    sizes = np.clip(np.exp(np.log(64 << 10) + 2.0 * rng.standard_normal(npool)), 4 << 10, 256 << 20).astype(np.uint64)
+    kinds = [("mixed", "review", "log")[i % 3] for i in range(npool)]
+    seeds = (synth.BASE_SEED + 5) * 1000 + np.arange(npool, dtype=np.uint64)
+    host = torch.empty(int(sizes.sum()), dtype=torch.uint8, pin_memory=True)
+    offs, lens, rows = synth.generate_batch_into(kinds, seeds, sizes, host.data_ptr())
+    data = host.to(dev)
+    parsers = {k: Parser(formats.by_name(synth.DIALECT[k]), synth.SCHEMAS[k]) for k in ("mixed", "review", "log")}
+    rate = args.serve_rate
+    nreq = int(rate * args.serve_seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    picks = rng.integers(0, npool, nreq)
+
+    def make():
+        reqs = []
+        for j, i in enumerate(picks):
+            p = parsers[kinds[i]]
+            d = data[int(offs[i]): int(offs[i]) + int(lens[i])]
+            reqs.append(Request(j, p, d, max(int(rows[i]), 1), [max(int(lens[i]), 1)] * len(p.types)))
+        return reqs
+
+    served = run_trace(Server(arena_bytes=40 << 30, streams=4, device=dev), make(), arrivals)
+    plain = run_trace_plain(make(), arrivals, device=dev)
+    log(f"served: {served}; plain: {plain}")
+    return {"value": served["gbs"], "unit": "GB/s", "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"],
+            "requests": nreq, "seconds": args.serve_seconds, "rate_per_s": rate, "rounds": served["rounds"],
+            "wall_s": served["wall_s"], "plain": plain,
+            "workload": f"Poisson {rate}/s for {args.serve_seconds} s; log-normal sizes 4 KB..256 MB (median 64 KB); "
+                        f"pool of {npool} mixed-CSV / review-CSV / web-log payloads; 40 GB arena"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,6 +313,14 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--partition-bytes", type=int, default=256 << 20)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-inputs", type=int, default=10_000)
+    ap.add_argument("--batch-bytes", type=int, default=6_000_000_000)
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-pool", type=int, default=1500)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -268,44 +404,45 @@ def main():
     traffic = recorded_traffic(args.workload)
 
     # ------------------------------------------------- end to end (host)
+    # Through the streaming public API: pinned host input -> device, parse,
+    # columns -> pinned host memory, partitions overlapped (Sec. 4.4).
     e2e = None
     if not args.no_e2e:
-        host_out = []
-        d2h = 0
-        for t_ in [*out.values, *[o for o in out.offsets if o is not None], *out.validity, out.row_valid,
-                   out.result_buf]:
-            host_out.append((t_, torch.empty(t_.shape, dtype=t_.dtype, pin_memory=True)))
-            d2h += t_.numel() * t_.element_size()
-        dev_in = torch.empty_like(data)
+        from paper_1905_13415_gb300.stream import StreamParser
+
+        del out
+        torch.cuda.empty_cache()
+        sp = StreamParser(parser, partition_bytes=args.partition_bytes, device=dev)
 
         def e2e_step():
-            dev_in.copy_(host_in, non_blocking=True)
-            parser.parse_into(dev_in, out, stream=stream)
-            for d, h in host_out:
-                h.copy_(d, non_blocking=True)
+            parts = sp.parse(host_in)
+            return sum(x.rows for x in parts), parts
 
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
-        torch.cuda.synchronize()
+        for _ in range(max(1, min(args.warmup, 2))):
+            got_rows, parts = e2e_step()
+        assert got_rows == rows, (got_rows, rows)
+        d2h = sum(sum(v.numel() * v.element_size() for v in col.values()) + x.row_valid.numel()
+                  for x in parts for col in x.columns)
+        del parts
         if world > 1:
             torch.distributed.barrier()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        ksteps = max(3, min(args.steps, 10))
-        s0.record(stream)
-        for _ in range(ksteps):
-            e2e_step()
-        s1.record(stream)
+        ksteps = max(2, min(args.steps, 5))
         torch.cuda.synchronize()
-        e2e_ms = s0.elapsed_time(s1) / ksteps
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            got_rows, parts = e2e_step()
+            del parts
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / ksteps
         if world > 1:
             t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e2e_ms = float(t[0])
         e2e = {"value": round(world * n / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
-               "h2d_bytes_per_step": n, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
-               "steps": ksteps}
-        del dev_in
+               "h2d_bytes_per_step": n, "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
+               "steps": ksteps, "api": "StreamParser.parse (partitioned, overlapped, carry-over)",
+               "partition_bytes": args.partition_bytes}
+        del sp
 
     # ------------------------------------------------------ CPU baseline
     cpu = None
@@ -317,6 +454,15 @@ def main():
         rate, secs = oracle_rate(wl, raw[:last], schema, dialect)
         cpu = {"value": round(rate, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {last} bytes (whole records) of the same input, {secs:.1f} s single-threaded"}
+
+    def log(msg):
+        print(msg, file=sys.stderr, flush=True)
+
+    batched = served = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batched = run_batched(args, dev, log)
+    if rank == 0 and world == 1 and not args.no_serve:
+        served = run_served(args, dev, log)
 
     if rank == 0:
         line = {
@@ -335,6 +481,8 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
+            "batched": batched,
+            "served": served,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -140,6 +140,7 @@ typedef struct pp_column {
  *                        from the schema, or a numeric field did not convert)
  *   first_invalid_offset first byte whose transition enters the invalid
  *                        state, or -1
+ *   consumed             see PP_OPT_PARTIAL_INPUT
  *   values_bytes_needed  per STRING column, data bytes the input holds for it
  *                        (the values_cap that is enough), else 0 */
 typedef struct pp_parse_result {
@@ -148,6 +149,8 @@ typedef struct pp_parse_result {
   int64_t rows;
   int64_t n_rejected;
   int64_t first_invalid_offset;
+  int64_t consumed;  /* PP_OPT_PARTIAL_INPUT: bytes up to and including the
+                        last record delimiter; else len */
   int64_t values_bytes_needed[PP_MAX_COLUMNS];
 } pp_parse_result;
 
@@ -168,11 +171,19 @@ typedef struct pp_parser pp_parser;
 
 /* Tuning options (parparaw_set_option). */
 typedef enum pp_option {
-  PP_OPT_TILE_CONFIG = 1,   /* 0 = default tile; 1 = 512-byte test tile;
-                               2 = 3 KiB tile; 3 = 28 KiB tile */
+  PP_OPT_TILE_CONFIG = 1,   /* tile shape, threads x bytes per thread:
+                               0 = default (3); 1 = 32x16 (test); 2 = 64x48;
+                               3 = 256x112; 4 = 128x208; 5 = 128x112;
+                               6 = 128x112 (6 blocks/SM); 7 = 128x48;
+                               8 = 256x80 */
   PP_OPT_TIMEOUT_MS = 2,    /* bound of every device-side wait (default 2000) */
-  PP_OPT_GRID_LIMIT = 3     /* 0 = one block per tile; n = at most n resident
+  PP_OPT_GRID_LIMIT = 3,    /* 0 = one block per tile; n = at most n resident
                                blocks looping over tiles (persistent) */
+  PP_OPT_PARTIAL_INPUT = 4  /* 1 = the input is one partition of a longer
+                               stream (Sec. 4.4): bytes after the last record
+                               delimiter are an incomplete record, not emitted
+                               and not an error; result.consumed reports where
+                               they start.  0 (default) = the input is whole. */
 } pp_option;
 
 typedef struct pp_parser_info {
@@ -226,6 +237,27 @@ typedef struct pp_batch_item {
  * the call returns.  The tile configuration of the batch is that of the first
  * item's parser. */
 pp_status parparaw_parse_batch(const pp_batch_item* items, uint64_t n, void* stream);
+
+/* A prepared batch: the items' descriptors (the device-side work queue of
+ * (input, tile) items, tables, output columns) and their scratch, uploaded
+ * once to device memory so that each parparaw_batch_launch is kernel
+ * launches only.  The items' inputs and outputs must stay valid while the
+ * batch is launched; their contents may change between launches. */
+typedef struct pp_batch pp_batch;
+
+/* Validates the items as parparaw_parse_batch does, allocates the batch's
+ * device memory (cudaMalloc) and uploads its descriptors (synchronous copy).
+ * `items` is host memory read before the call returns.  *out is owned by the
+ * caller and released with parparaw_batch_destroy. */
+pp_status parparaw_batch_create(const pp_batch_item* items, uint64_t n, pp_batch** out);
+
+/* Enqueues one parse of every item of the batch on `stream` (init kernel,
+ * one persistent tile kernel over all items' tiles, finalize kernel).  Launches
+ * of one batch must not overlap on the device: they share its scratch. */
+pp_status parparaw_batch_launch(pp_batch* batch, void* stream);
+
+/* Frees the batch (cudaFree: call it once its launches have completed). */
+void parparaw_batch_destroy(pp_batch* batch);
 
 /* Size of the fixed device scratch behind parparaw_parse_noalloc. */
 #define PP_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -18,11 +18,12 @@ STRING, INT32, INT64, FLOAT64, TIMESTAMP_S, DATE_D, TIMESTAMP_CLF = range(7)
 TYPE_NAMES = {"string": STRING, "int32": INT32, "int64": INT64, "float64": FLOAT64,
               "timestamp": TIMESTAMP_S, "date": DATE_D, "timestamp_clf": TIMESTAMP_CLF}
 
-OPT_TILE_CONFIG, OPT_TIMEOUT_MS, OPT_GRID_LIMIT = 1, 2, 3
+OPT_TILE_CONFIG, OPT_TIMEOUT_MS, OPT_GRID_LIMIT, OPT_PARTIAL_INPUT = 1, 2, 3, 4
 
 EXPORTED = ["parparaw_create", "parparaw_destroy", "parparaw_set_option", "parparaw_get_info",
             "parparaw_parse", "parparaw_parse_batch", "parparaw_set_kernel_events",
-            "parparaw_status_string", "parparaw_parse_noalloc"]
+            "parparaw_status_string", "parparaw_parse_noalloc", "parparaw_batch_create",
+            "parparaw_batch_launch", "parparaw_batch_destroy"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -51,7 +52,7 @@ class pp_column(ctypes.Structure):
 class pp_parse_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("final_state", ctypes.c_int32),
                 ("rows", ctypes.c_int64), ("n_rejected", ctypes.c_int64),
-                ("first_invalid_offset", ctypes.c_int64),
+                ("first_invalid_offset", ctypes.c_int64), ("consumed", ctypes.c_int64),
                 ("values_bytes_needed", ctypes.c_int64 * MAX_COLUMNS)]
 
 
@@ -104,6 +105,12 @@ def load():
     L.parparaw_get_info.restype = ctypes.c_int
     L.parparaw_parse.argtypes = [vp, vp, ctypes.c_uint64, ctypes.POINTER(pp_columns), vp]
     L.parparaw_parse.restype = ctypes.c_int
+    L.parparaw_batch_create.argtypes = [ctypes.POINTER(pp_batch_item), ctypes.c_uint64, ctypes.POINTER(vp)]
+    L.parparaw_batch_create.restype = ctypes.c_int
+    L.parparaw_batch_launch.argtypes = [vp, vp]
+    L.parparaw_batch_launch.restype = ctypes.c_int
+    L.parparaw_batch_destroy.argtypes = [vp]
+    L.parparaw_batch_destroy.restype = None
     L.parparaw_parse_noalloc.argtypes = [vp, vp, ctypes.c_uint64, ctypes.POINTER(pp_columns), vp]
     L.parparaw_parse_noalloc.restype = ctypes.c_int
     L.parparaw_parse_batch.argtypes = [ctypes.POINTER(pp_batch_item), ctypes.c_uint64, vp]

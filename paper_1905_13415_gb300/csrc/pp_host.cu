@@ -55,6 +55,7 @@ __global__ void pp_init_kernel(const __grid_constant__ Launch L) {
       M->done = 0;
       M->rows = 0;
       M->final_state = TB.start_state;
+      M->last_record_end = 0;
       for (int k = 0; k < PP_MAX_STRING_COLUMNS; ++k) M->bytes_total[k] = 0;
       J.result->n_rejected = 0;
     }
@@ -121,11 +122,12 @@ __global__ void pp_finalize_kernel(const __grid_constant__ Launch L) {
       if (M.timeout || !ok_run) status = PP_E_TIMEOUT;
       else if (cap) status = PP_E_CAPACITY;
       else if (M.first_invalid != ~0ull) status = PP_E_INVALID_INPUT;
-      else if (!((TB.accept_mask >> M.final_state) & 1u)) status = PP_E_UNTERMINATED;
+      else if (!TB.partial && !((TB.accept_mask >> M.final_state) & 1u)) status = PP_E_UNTERMINATED;
       res->status = status;
       res->final_state = M.final_state;
       res->rows = R;
       res->first_invalid_offset = M.first_invalid == ~0ull ? -1 : static_cast<int64_t>(M.first_invalid);
+      res->consumed = TB.partial ? static_cast<int64_t>(M.last_record_end) : static_cast<int64_t>(J.len);
     }
     __syncthreads();
   }
@@ -150,6 +152,7 @@ ShapeInfo shape_for(int cfg) {
     case 5: return shape_info_m128();
     case 6: return shape_info_m128x6();
     case 7: return shape_info_s128();
+    case 8: return shape_info_mid3();
     default: return shape_info_mid();
   }
 }
@@ -453,7 +456,7 @@ extern "C" pp_status parparaw_set_option(pp_parser* P, pp_option option, int64_t
   if (P == nullptr) return PP_E_ARG;
   switch (option) {
     case PP_OPT_TILE_CONFIG:
-      if (value < 0 || value > 7) return PP_E_ARG;
+      if (value < 0 || value > 8) return PP_E_ARG;
       P->tile_config = static_cast<int>(value);
       return PP_OK;
     case PP_OPT_TIMEOUT_MS:
@@ -463,6 +466,10 @@ extern "C" pp_status parparaw_set_option(pp_parser* P, pp_option option, int64_t
     case PP_OPT_GRID_LIMIT:
       if (value < 0) return PP_E_ARG;
       P->grid_limit = value;
+      return PP_OK;
+    case PP_OPT_PARTIAL_INPUT:
+      if (value != 0 && value != 1) return PP_E_ARG;
+      P->tab.partial = static_cast<uint8_t>(value);
       return PP_OK;
     default:
       return PP_E_ARG;
@@ -540,80 +547,128 @@ extern "C" pp_status parparaw_parse(const pp_parser* P, const uint8_t* input, ui
   return st;
 }
 
-extern "C" pp_status parparaw_parse_batch(const pp_batch_item* items, uint64_t n, void* stream_) {
-  if (items == nullptr && n > 0) return PP_E_ARG;
-  if (n == 0) return PP_OK;
-  if (n > 0xFFFFFFFFull) return PP_E_UNSUPPORTED;
-  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-  const pp_parser* first = items[0].parser;
-  if (first == nullptr) return PP_E_ARG;
-  const ShapeInfo shape = shape_for(first->tile_config);
+namespace pp {
+namespace {
 
+// Host-side description of a batch: unique parser tables, one job per item,
+// the items' columns, and where every piece lives in one device allocation
+// laid out as [per-job scratch][tables][jobs][columns].
+struct BatchPlan {
   std::vector<Tables> tables;
-  std::unordered_map<const pp_parser*, uint32_t> table_index;
-  std::vector<Job> jobs(n);
+  std::vector<Job> jobs;
   std::vector<Col> cols;
-  std::vector<ScratchPlan> plans(n);
+  std::vector<ScratchPlan> plans;
+  const pp_parser* first = nullptr;
+  ShapeInfo shape;
   int nspec = 4;
   uint64_t total_tiles = 0, max_tiles = 0, max_words = 0;
+  size_t off_tables = 0, off_jobs = 0, off_cols = 0, total = 0;
+};
+
+pp_status plan_batch(const pp_batch_item* items, uint64_t n, BatchPlan* bp) {
+  if (items == nullptr || n == 0) return PP_E_ARG;
+  if (n > 0xFFFFFFFFull) return PP_E_UNSUPPORTED;
+  bp->first = items[0].parser;
+  if (bp->first == nullptr) return PP_E_ARG;
+  bp->shape = shape_for(bp->first->tile_config);
+  std::unordered_map<const pp_parser*, uint32_t> table_index;
+  bp->jobs.resize(n);
+  bp->plans.resize(n);
   size_t scratch_bytes = 64;
   for (uint64_t i = 0; i < n; ++i) {
     const pp_batch_item& it = items[i];
     if (it.parser == nullptr || (it.input == nullptr && it.len > 0)) return PP_E_ARG;
-    pp_status st = check_columns(it.parser, it.out);
+    const pp_status st = check_columns(it.parser, it.out);
     if (st != PP_OK) return st;
     auto found = table_index.find(it.parser);
     uint32_t ti;
     if (found == table_index.end()) {
-      ti = static_cast<uint32_t>(tables.size());
-      tables.push_back(it.parser->tab);
+      ti = static_cast<uint32_t>(bp->tables.size());
+      bp->tables.push_back(it.parser->tab);
       table_index[it.parser] = ti;
-      nspec = std::max(nspec, nspec_of(it.parser->tab));
+      bp->nspec = std::max(bp->nspec, nspec_of(it.parser->tab));
     } else {
       ti = found->second;
     }
-    Job& J = jobs[i];
+    Job& J = bp->jobs[i];
     std::memset(&J, 0, sizeof(J));
     J.input = it.input;
     J.len = it.len;
     J.head = it.len > 0 ? (reinterpret_cast<uintptr_t>(it.input) & 15u) : 0;
-    J.ntiles = it.len > 0 ? (J.head + it.len + shape.tile_bytes - 1) / shape.tile_bytes : 0;
-    J.tile_base = total_tiles;
+    J.ntiles = it.len > 0 ? (J.head + it.len + bp->shape.tile_bytes - 1) / bp->shape.tile_bytes : 0;
+    J.tile_base = bp->total_tiles;
     J.rows_cap = it.out->rows_cap;
     J.bit_words = (it.out->rows_cap + 31) / 32 + 1;
     J.row_valid = it.out->row_valid;
     J.result = it.out->result;
     J.tables = ti;
-    J.col0 = static_cast<uint32_t>(cols.size());
+    J.col0 = static_cast<uint32_t>(bp->cols.size());
     for (uint32_t c = 0; c < it.out->num_columns; ++c) {
       Col col;
       col.values = it.out->cols[c].values;
       col.offsets = it.out->cols[c].offsets;
       col.validity = it.out->cols[c].validity;
       col.values_cap = it.out->cols[c].values_cap;
-      cols.push_back(col);
+      bp->cols.push_back(col);
     }
-    plans[i] = plan_scratch(scratch_bytes, J.ntiles, it.parser->tab.num_str, it.parser->tab.num_num,
-                            J.bit_words);
-    scratch_bytes = plans[i].total;
-    total_tiles += J.ntiles;
-    max_tiles = std::max(max_tiles, J.ntiles);
-    max_words = std::max(max_words, J.bit_words);
+    bp->plans[i] = plan_scratch(scratch_bytes, J.ntiles, it.parser->tab.num_str, it.parser->tab.num_num,
+                                J.bit_words);
+    scratch_bytes = bp->plans[i].total;
+    bp->total_tiles += J.ntiles;
+    bp->max_tiles = std::max(bp->max_tiles, J.ntiles);
+    bp->max_words = std::max(bp->max_words, J.bit_words);
   }
-  const size_t off_tables = align_up(scratch_bytes, 256);
-  const size_t off_jobs = align_up(off_tables + sizeof(Tables) * tables.size(), 256);
-  const size_t off_cols = align_up(off_jobs + sizeof(Job) * jobs.size(), 256);
-  const size_t total = align_up(off_cols + sizeof(Col) * cols.size(), 256);
+  bp->off_tables = align_up(scratch_bytes, 256);
+  bp->off_jobs = align_up(bp->off_tables + sizeof(Tables) * bp->tables.size(), 256);
+  bp->off_cols = align_up(bp->off_jobs + sizeof(Job) * bp->jobs.size(), 256);
+  bp->total = align_up(bp->off_cols + sizeof(Col) * bp->cols.size(), 256);
+  return PP_OK;
+}
+
+// Points the jobs at their scratch in `dev` and packs tables, jobs and
+// columns into one host image of the device region starting at off_tables.
+void pack_batch(BatchPlan& bp, uint8_t* dev, std::vector<uint8_t>* image) {
+  for (size_t i = 0; i < bp.jobs.size(); ++i) fill_job(bp.jobs[i], bp.plans[i], dev);
+  image->assign(bp.total - bp.off_tables, 0);
+  std::memcpy(image->data(), bp.tables.data(), sizeof(Tables) * bp.tables.size());
+  std::memcpy(image->data() + (bp.off_jobs - bp.off_tables), bp.jobs.data(), sizeof(Job) * bp.jobs.size());
+  std::memcpy(image->data() + (bp.off_cols - bp.off_tables), bp.cols.data(), sizeof(Col) * bp.cols.size());
+}
+
+void batch_launch_params(const BatchPlan& bp, uint8_t* dev, Launch* L) {
+  std::memset(L, 0, sizeof(*L));
+  L->tables = reinterpret_cast<const Tables*>(dev + bp.off_tables);
+  L->jobs = reinterpret_cast<const Job*>(dev + bp.off_jobs);
+  L->cols = reinterpret_cast<const Col*>(dev + bp.off_cols);
+  L->njobs = static_cast<uint32_t>(bp.jobs.size());
+  L->total_tiles = bp.total_tiles;
+  L->work_counter = reinterpret_cast<unsigned long long*>(dev);
+  L->timeout_ns = bp.first->timeout_ns;
+}
+
+}  // namespace
+}  // namespace pp
+
+struct pp_batch {
+  pp::BatchPlan plan;
+  uint8_t* dev = nullptr;
+  pp::Launch* launch = nullptr;
+};
+
+extern "C" pp_status parparaw_parse_batch(const pp_batch_item* items, uint64_t n, void* stream_) {
+  if (items == nullptr && n > 0) return PP_E_ARG;
+  if (n == 0) return PP_OK;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  BatchPlan bp;
+  pp_status st = plan_batch(items, n, &bp);
+  if (st != PP_OK) return st;
   uint8_t* scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), total, stream);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bp.total, stream);
   if (e != cudaSuccess) return map_err(e);
-  for (uint64_t i = 0; i < n; ++i) fill_job(jobs[i], plans[i], scratch);
-  // one host staging buffer, copied in one transfer
-  std::vector<uint8_t> host(total - off_tables);
-  std::memcpy(host.data(), tables.data(), sizeof(Tables) * tables.size());
-  std::memcpy(host.data() + (off_jobs - off_tables), jobs.data(), sizeof(Job) * jobs.size());
-  std::memcpy(host.data() + (off_cols - off_tables), cols.data(), sizeof(Col) * cols.size());
-  e = cudaMemcpyAsync(scratch + off_tables, host.data(), host.size(), cudaMemcpyHostToDevice, stream);
+  std::vector<uint8_t> image;
+  pack_batch(bp, scratch, &image);
+  // pageable source: staged by the runtime before the call returns
+  e = cudaMemcpyAsync(scratch + bp.off_tables, image.data(), image.size(), cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) {
     cudaFreeAsync(scratch, stream);
     return map_err(e);
@@ -623,20 +678,57 @@ extern "C" pp_status parparaw_parse_batch(const pp_batch_item* items, uint64_t n
     cudaFreeAsync(scratch, stream);
     return PP_E_NOMEM;
   }
-  Launch& L = *Lp;
-  std::memset(&L, 0, sizeof(L));
-  L.tables = reinterpret_cast<const Tables*>(scratch + off_tables);
-  L.jobs = reinterpret_cast<const Job*>(scratch + off_jobs);
-  L.cols = reinterpret_cast<const Col*>(scratch + off_cols);
-  L.njobs = static_cast<uint32_t>(n);
-  L.total_tiles = total_tiles;
-  L.work_counter = reinterpret_cast<unsigned long long*>(scratch);
-  L.timeout_ns = first->timeout_ns;
-  pp_status st = run_launch(L, shape, nspec, first->grid_limit, first, stream,
-                            static_cast<uint32_t>(std::min<uint64_t>(n, 65535)), max_tiles, max_words);
+  batch_launch_params(bp, scratch, Lp);
+  st = run_launch(*Lp, bp.shape, bp.nspec, bp.first->grid_limit, bp.first, stream,
+                  static_cast<uint32_t>(std::min<uint64_t>(n, 65535)), bp.max_tiles, bp.max_words);
   cudaFreeAsync(scratch, stream);
   delete Lp;
   return st;
+}
+
+extern "C" pp_status parparaw_batch_create(const pp_batch_item* items, uint64_t n, pp_batch** out) {
+  if (out == nullptr) return PP_E_ARG;
+  *out = nullptr;
+  pp_batch* b = new (std::nothrow) pp_batch();
+  if (b == nullptr) return PP_E_NOMEM;
+  pp_status st = plan_batch(items, n, &b->plan);
+  if (st != PP_OK) {
+    delete b;
+    return st;
+  }
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->dev), b->plan.total);
+  if (e != cudaSuccess) {
+    delete b;
+    return map_err(e);
+  }
+  std::vector<uint8_t> image;
+  pack_batch(b->plan, b->dev, &image);
+  e = cudaMemcpy(b->dev + b->plan.off_tables, image.data(), image.size(), cudaMemcpyHostToDevice);
+  b->launch = new (std::nothrow) Launch();
+  if (e != cudaSuccess || b->launch == nullptr) {
+    cudaFree(b->dev);
+    delete b->launch;
+    delete b;
+    return e != cudaSuccess ? map_err(e) : PP_E_NOMEM;
+  }
+  batch_launch_params(b->plan, b->dev, b->launch);
+  *out = b;
+  return PP_OK;
+}
+
+extern "C" pp_status parparaw_batch_launch(pp_batch* b, void* stream_) {
+  if (b == nullptr) return PP_E_ARG;
+  const BatchPlan& bp = b->plan;
+  return run_launch(*b->launch, bp.shape, bp.nspec, bp.first->grid_limit, bp.first,
+                    static_cast<cudaStream_t>(stream_),
+                    static_cast<uint32_t>(std::min<uint64_t>(bp.jobs.size(), 65535)), bp.max_tiles, bp.max_words);
+}
+
+extern "C" void parparaw_batch_destroy(pp_batch* b) {
+  if (b == nullptr) return;
+  cudaFree(b->dev);
+  delete b->launch;
+  delete b;
 }
 
 // ================================================= allocation-free parse ===

@@ -66,9 +66,6 @@ struct TileShape {
   static constexpr int MW = (B + 63) / 64; // 64-bit mask words per chunk
   static constexpr int NW = NT / 32;
   static constexpr int kStage = T + 32 * PP_MAX_STRING_COLUMNS + 64;
-  // numeric fields queued per tile for the block-wide conversion pass; a tile
-  // with more falls back to converting the rest inline
-  static constexpr int kConvCap = T / 8;
 };
 
 struct SmemHead {
@@ -88,6 +85,8 @@ struct SmemHead {
   uint8_t str_col[PP_MAX_STRING_COLUMNS];  // slot -> column
   int32_t job_loaded;
   uint32_t nconv;
+  unsigned long long tile_last_rd;  // partial inputs: last record delimiter + 1
+  uint32_t conv_base, conv_cap;  // queue of numeric fields in the staging buffer's free tail
   long long ph_cycles[10];  // profiling builds only
   Job jd;                  // the current job and its columns, staged from the
   Col cd[PP_MAX_COLUMNS];  // launch parameters / global memory once per job
@@ -101,9 +100,7 @@ struct SmemLayout {
   static constexpr size_t kDm = kStage + ((Shape::kStage + 127) & ~size_t(127));
   static constexpr size_t kDl = kDm + sizeof(uint64_t) * Shape::NT * Shape::MW;
   static constexpr size_t kCnt = kDl + sizeof(uint64_t) * Shape::NT * Shape::MW;
-  static constexpr size_t kConvA = kCnt + sizeof(uint16_t) * Shape::NT * PP_MAX_STRING_COLUMNS;
-  static constexpr size_t kConvB = kConvA + sizeof(uint32_t) * Shape::kConvCap;
-  static constexpr size_t kBytes = kConvB + sizeof(uint16_t) * Shape::kConvCap;
+  static constexpr size_t kBytes = kCnt + sizeof(uint16_t) * Shape::NT * PP_MAX_STRING_COLUMNS;
 };
 
 // ---------------------------------------------------- look-back (1 word) ---
@@ -245,7 +242,9 @@ struct BitIter {
   }
 };
 
-// shared -> shared byte copy with 32-bit stores where the destination allows
+// shared -> shared byte copy: bytes up to a 4-byte aligned destination, then
+// 32-bit words assembled with funnel shifts, four per step (the source loads
+// of a step are independent).  May read up to 20 bytes past the source end.
 __device__ __forceinline__ void smem_copy(uint8_t* dst, const uint8_t* src, int n) {
   while (n > 0 && (reinterpret_cast<uintptr_t>(dst) & 3)) {
     *dst++ = *src++;
@@ -256,15 +255,20 @@ __device__ __forceinline__ void smem_copy(uint8_t* dst, const uint8_t* src, int 
     const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 3) * 8;
     const uint32_t* s = reinterpret_cast<const uint32_t*>(reinterpret_cast<uintptr_t>(src) & ~uintptr_t(3));
     uint32_t* d = reinterpret_cast<uint32_t*>(dst);
-    if (sh == 0) {
-      for (int k = 0; k < nw; ++k) d[k] = s[k];
-    } else {
-      uint32_t lo = s[0];
-      for (int k = 0; k < nw; ++k) {
-        const uint32_t hi = s[k + 1];
-        d[k] = __funnelshift_r(lo, hi, sh);
-        lo = hi;
-      }
+    uint32_t lo = s[0];
+    int k = 0;
+    for (; k + 4 <= nw; k += 4) {
+      const uint32_t a = s[k + 1], b = s[k + 2], c = s[k + 3], e = s[k + 4];
+      d[k] = __funnelshift_r(lo, a, sh);
+      d[k + 1] = __funnelshift_r(a, b, sh);
+      d[k + 2] = __funnelshift_r(b, c, sh);
+      d[k + 3] = __funnelshift_r(c, e, sh);
+      lo = e;
+    }
+    for (; k < nw; ++k) {
+      const uint32_t hi = s[k + 1];
+      d[k] = __funnelshift_r(lo, hi, sh);
+      lo = hi;
     }
     dst += 4 * nw;
     src += 4 * nw;
@@ -293,8 +297,6 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
   uint64_t* s_dm = reinterpret_cast<uint64_t*>(smem + Lay::kDm);
   uint64_t* s_dl = reinterpret_cast<uint64_t*>(smem + Lay::kDl);
   uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + Lay::kCnt);
-  uint32_t* s_conv_a = reinterpret_cast<uint32_t*>(smem + Lay::kConvA);  // start | column << 16
-  uint16_t* s_conv_b = reinterpret_cast<uint16_t*>(smem + Lay::kConvB);  // row - first row of tile
   const Tables& TB = H->tab;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -328,6 +330,9 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       H->item = item;
       H->job = j;
       H->nconv = 0;
+      H->tile_last_rd = 0;
+      H->conv_base = 0;  // no string bytes staged: the whole buffer is free
+      H->conv_cap = static_cast<uint32_t>(Shape::kStage) / 6u;
     }
     __syncthreads();
     const unsigned long long item = H->item;
@@ -554,11 +559,15 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       }
 #pragma unroll
       for (int w = 0; w < MW; ++w) ncol += __popcll(fm[w] & ~bits_below(last_rd + 1 - 64 * w));
+      if (TB.partial && last_rd >= 0)
+        atomicMax(&H->tile_last_rd, static_cast<unsigned long long>(cv0 + last_rd + 1 - static_cast<int64_t>(J.head)));
     }
     uint32_t rc_tile;
     const uint32_t rc_ex = block_exclusive_scan<NT>(rc_pack(nrec, ncol, nrec > 0), rc_combine,
                                                     rc_pack(0, 0, false), H->wsum32, &rc_tile);
     PP_PHASE(4);
+    if (TB.partial && tid == 0 && H->tile_last_rd)  // after the scan's barriers
+      atomicMax(&J.misc->last_record_end, H->tile_last_rd);
     if (warp == 0) {
       const uint64_t agg = tc_pack(rc_tile & 0xFFFFu, (rc_tile >> 16) & kColSat, (rc_tile >> 31) != 0);
       const uint64_t pre = lookback_word<RcPolicy>(J.st_rc, t, agg, tc_pack(0, 0, true), deadline, J.misc);
@@ -685,6 +694,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
             H->stage_off[k] = off;
             off += H->tile_tot[k];
           }
+          H->conv_base = (off + 3u) & ~3u;
+          H->conv_cap = (static_cast<uint32_t>(Shape::kStage) - H->conv_base) / 6u;
         }
       }
       __syncthreads();
@@ -776,6 +787,13 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       }
     };
     auto stage_piece = [&](uint32_t slot, int a, int b) {
+      if (a >= b) return;
+      if (popc_range(dm, a, b) == b - a) {  // all data: one copy (text fields)
+        const uint32_t at = H->stage_off[slot] + s_cnt[slot * NT + tid];
+        smem_copy(s_stage + at, chunk + a, b - a);
+        s_cnt[slot * NT + tid] = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (b - a));
+        return;
+      }
       int x = a;
       while (x < b) {
         const int rs = next_bit(dm, x, b, true);
@@ -797,7 +815,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       uint64_t r = row_start;
       int pos = lo;
       const bool eof_here = last_tile && lo < hi && cv0 + hi == static_cast<int64_t>(VL);
-      bool trailing = eof_here && !test_bit(rm, hi - 1) && ((TB.accept_mask >> s_end) & 1u);
+      bool trailing = eof_here && !TB.partial && !test_bit(rm, hi - 1) && ((TB.accept_mask >> s_end) & 1u);
       bool opens = t == 0 && tid == 0 && J.len > 0;  // the input's first field
       uint64_t dl[MW];
 #pragma unroll
@@ -806,9 +824,11 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       for (;;) {
         if (opens && c < C && TB.num_slot[c] != 0xFF && r < rows_cap) {
           const uint32_t slot_i = atomicAdd(&H->nconv, 1u);
-          if (slot_i < static_cast<uint32_t>(Shape::kConvCap)) {
-            s_conv_a[slot_i] = static_cast<uint32_t>(tid * B + pos) | (c << 16);
-            s_conv_b[slot_i] = static_cast<uint16_t>(r - tile_row0);
+          if (slot_i < H->conv_cap) {
+            uint32_t* qa = reinterpret_cast<uint32_t*>(s_stage + H->conv_base);  // start | column << 16
+            uint16_t* qb = reinterpret_cast<uint16_t*>(qa + H->conv_cap);        // row - first row of tile
+            qa[slot_i] = static_cast<uint32_t>(tid * B + pos) | (c << 16);
+            qb[slot_i] = static_cast<uint16_t>(r - tile_row0);
           } else {
             convert_at(r, c, tid * B + pos);
           }
@@ -855,10 +875,12 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     // --------------------- a7: queued numeric fields, one per thread
     __syncthreads();
     {
-      const uint32_t nq = min(H->nconv, static_cast<uint32_t>(Shape::kConvCap));
+      const uint32_t nq = min(H->nconv, H->conv_cap);
+      const uint32_t* qa = reinterpret_cast<const uint32_t*>(s_stage + H->conv_base);
+      const uint16_t* qb = reinterpret_cast<const uint16_t*>(qa + H->conv_cap);
       for (uint32_t i = tid; i < nq; i += NT) {
-        const uint32_t a = s_conv_a[i];
-        convert_at(tile_row0 + s_conv_b[i], a >> 16, static_cast<int>(a & 0xFFFFu));
+        const uint32_t a = qa[i];
+        convert_at(tile_row0 + qb[i], a >> 16, static_cast<int>(a & 0xFFFFu));
       }
     }
 

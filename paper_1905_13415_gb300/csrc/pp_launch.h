@@ -20,5 +20,6 @@ ShapeInfo shape_info_wide();    // 128 threads x 208 B = 26 KiB tiles
 ShapeInfo shape_info_m128();    // 128 threads x 112 B = 14 KiB tiles, 4 blocks / SM
 ShapeInfo shape_info_m128x6();  // 128 threads x 112 B = 14 KiB tiles, 6 blocks / SM
 ShapeInfo shape_info_s128();    // 128 threads x 48 B  =  6 KiB tiles, 8 blocks / SM
+ShapeInfo shape_info_mid3();    // 256 threads x 80 B  = 20 KiB tiles, 3 blocks / SM
 
 }  // namespace pp

@@ -18,7 +18,7 @@ struct Tables {
   uint8_t num_slot[PP_MAX_COLUMNS];    // numeric column -> slot, else 0xFF
   uint8_t num_states, num_groups, num_symbols, catch_all;
   uint8_t start_state, invalid_state, idempotent, num_columns;
-  uint8_t num_str, num_num, pad0, pad1;
+  uint8_t num_str, num_num, partial, pad1;  // partial: more input follows
   uint32_t accept_mask;
 };
 
@@ -37,6 +37,7 @@ struct Misc {
   int64_t rows;                      // records emitted
   int32_t final_state;
   uint32_t pad;
+  unsigned long long last_record_end;  // partial inputs: atomicMax of (last RD + 1)
   int64_t bytes_total[PP_MAX_STRING_COLUMNS];
 };
 

@@ -44,6 +44,7 @@ class Result:
     n_rejected: int
     first_invalid_offset: int
     values_bytes_needed: list
+    consumed: int = 0
 
     @property
     def ok(self) -> bool:
@@ -96,7 +97,7 @@ class Output:
         raw = self.result_buf.cpu().numpy().tobytes()
         r = _abi.pp_parse_result.from_buffer_copy(raw)
         return Result(r.status, r.final_state, r.rows, r.n_rejected, r.first_invalid_offset,
-                      list(r.values_bytes_needed[: len(self.types)]))
+                      list(r.values_bytes_needed[: len(self.types)]), r.consumed)
 
     def output_bytes(self, rows: int) -> int:
         """Bytes of the fixed output layout for `rows` rows: values, int64
@@ -233,3 +234,40 @@ def parse_batch(items, stream=None) -> None:
     rc = lib.parparaw_parse_batch(arr, len(items), _stream(stream))
     if rc != _abi.OK:
         raise ParparawError(rc, "parparaw_parse_batch")
+
+
+class Batch:
+    """A prepared batch (parparaw_batch_create): descriptors uploaded once,
+    each launch() is kernel launches only."""
+
+    def __init__(self, items):
+        self._lib = _abi.load()
+        self.items = list(items)  # keeps parsers, inputs and outputs alive
+        arr = (_abi.pp_batch_item * len(self.items))()
+        for i, (p, data, out) in enumerate(self.items):
+            arr[i].parser = p.handle.value
+            arr[i].input = _ptr(data) if data.numel() else None
+            arr[i].len = data.numel()
+            arr[i].out = ctypes.pointer(out.desc)
+        handle = ctypes.c_void_p()
+        rc = self._lib.parparaw_batch_create(arr, len(self.items), ctypes.byref(handle))
+        if rc != _abi.OK:
+            raise ParparawError(rc, "parparaw_batch_create")
+        self.handle = handle
+
+    def launch(self, stream=None) -> None:
+        rc = self._lib.parparaw_batch_launch(self.handle, _stream(stream))
+        if rc != _abi.OK:
+            raise ParparawError(rc, "parparaw_batch_launch")
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize()
+            self._lib.parparaw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

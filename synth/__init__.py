@@ -78,6 +78,9 @@ def lib():
                                     ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
                                     ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
         L.synth_records.restype = ctypes.c_int
+        L.synth_generate_batch.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_uint64, ctypes.c_void_p,
+                                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.synth_generate_batch.restype = None
         _lib = L
     return _lib
 
@@ -115,3 +118,39 @@ def records(workload: str, seed: int, row0: int, nrows: int):
     t = bytes(truth[: tl.value])
     recs = [r.split(b"\x1f") for r in t.split(b"\x1e")[:-1]]
     return bytes(raw[: rl.value]), recs
+
+
+def batch_plan(n: int, total: int, seed: int, lo: int = 1 << 10, hi: int = 64 << 20, sigma: float = 2.0):
+    """Sizes and workloads of a batch: log-normal sizes clipped to [lo, hi] and
+    rescaled so they sum to about `total`; half CSV ('mixed'), half web logs."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.normal(0.0, sigma, n))
+    sizes = sizes / sizes.sum() * total
+    for _ in range(20):  # clip, then rescale the unclipped part
+        sizes = np.clip(sizes, lo, hi)
+        free = (sizes > lo) & (sizes < hi)
+        if not free.any():
+            break
+        fixed = sizes[~free].sum()
+        sizes[free] *= max(total - fixed, 0) / max(sizes[free].sum(), 1)
+    sizes = np.clip(sizes, lo, hi).astype(np.uint64)
+    kinds = ["mixed" if i % 2 == 0 else "log" for i in range(n)]
+    seeds = (seed * 1_000_003 + np.arange(n, dtype=np.uint64)).astype(np.uint64)
+    return sizes, kinds, seeds
+
+
+def generate_batch_into(kinds, seeds, targets, ptr: int, threads: int | None = None):
+    """Generates every input of a batch at host address ptr, input i at the
+    sum of the earlier targets.  Returns (offsets, lengths, rows)."""
+    n = len(kinds)
+    targets = np.asarray(targets, dtype=np.uint64)
+    offsets = np.zeros(n, dtype=np.uint64)
+    if n > 1:
+        offsets[1:] = np.cumsum(targets)[:-1]
+    wl = np.asarray([WORKLOADS[k] for k in kinds], dtype=np.int32)
+    seeds = np.asarray(seeds, dtype=np.uint64)
+    lens = np.zeros(n, dtype=np.uint64)
+    rows = np.zeros(n, dtype=np.uint64)
+    lib().synth_generate_batch(wl.ctypes.data, seeds.ctypes.data, targets.ctypes.data, offsets.ctypes.data, n,
+                               ptr, lens.ctypes.data, rows.ctypes.data, threads or min(32, os.cpu_count() or 1))
+    return offsets, lens, rows

@@ -466,3 +466,47 @@ int synth_records(int workload, uint64_t seed, uint64_t row0, uint64_t nrows, ui
   free(b.p);
   return rc;
 }
+
+/* ------------------------------------------------------ batches of inputs */
+typedef struct {
+  const int* workloads;
+  const uint64_t* seeds;
+  const uint64_t* targets;
+  const uint64_t* offsets; /* where input i starts in out */
+  uint8_t* out;
+  uint64_t* lens;
+  uint64_t* rows;
+  uint64_t n;
+  uint64_t next;
+  pthread_mutex_t mu;
+} batch_job_t;
+
+static void* batch_worker(void* arg) {
+  batch_job_t* b = (batch_job_t*)arg;
+  for (;;) {
+    pthread_mutex_lock(&b->mu);
+    uint64_t i = b->next++;
+    pthread_mutex_unlock(&b->mu);
+    if (i >= b->n) break;
+    uint64_t rows = 0;
+    int64_t len = synth_generate(b->workloads[i], b->seeds[i], b->targets[i], b->out + b->offsets[i],
+                                 b->targets[i], 1, &rows);
+    b->lens[i] = len < 0 ? 0 : (uint64_t)len;
+    b->rows[i] = rows;
+  }
+  return NULL;
+}
+
+/* Generates n independent inputs in parallel: input i (workload, seed) is the
+ * longest whole-record prefix of length <= targets[i], written at
+ * out + offsets[i] (the caller leaves targets[i] bytes there). */
+void synth_generate_batch(const int* workloads, const uint64_t* seeds, const uint64_t* targets,
+                          const uint64_t* offsets, uint64_t n, uint8_t* out, uint64_t* lens,
+                          uint64_t* rows, int threads) {
+  if (threads < 1) threads = 1;
+  batch_job_t b = {workloads, seeds, targets, offsets, out, lens, rows, n, 0, PTHREAD_MUTEX_INITIALIZER};
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
+  for (int t = 0; t < threads; ++t) pthread_create(&th[t], NULL, batch_worker, &b);
+  for (int t = 0; t < threads; ++t) pthread_join(th[t], NULL);
+  free(th);
+}
