@@ -133,10 +133,16 @@ __device__ __forceinline__ int window_take(uint32_t valid, uint32_t inc, bool* d
   return fi == 32 ? 32 : 0;
 }
 
+// Look-back windows: each lane loads kLbRounds status words at once, so one
+// round trip to L2 covers 32 * kLbRounds predecessors.  (A chain can resolve
+// at most one window of predecessors per round trip, which bounds how fast the
+// inclusive prefixes propagate through the tiles.)
+constexpr int kLbRounds = 4;
+
 // Called by one full warp.  Publishes the tile's aggregate, walks back over
-// predecessors (32 at a time) until an inclusive prefix is found, publishes
-// the tile's inclusive prefix and returns the exclusive one.  `first` is the
-// prefix of tile 0.  All waits end at `deadline` (then PP_E_TIMEOUT).
+// predecessors until an inclusive prefix is found, publishes the tile's
+// inclusive prefix and returns the exclusive one.  `first` is the prefix of
+// tile 0.  All waits end at `deadline` (then PP_E_TIMEOUT).
 template <class P>
 __device__ uint64_t lookback_word(uint64_t* st, uint64_t t, uint64_t agg, uint64_t first,
                                   uint64_t deadline, Misc* misc) {
@@ -148,39 +154,124 @@ __device__ uint64_t lookback_word(uint64_t* st, uint64_t t, uint64_t agg, uint64
   }
   if (lane == 0) st_relaxed_u64(&st[t], kFlagAgg | P::to_word(agg));
   uint64_t acc = P::kIdentity;
-  int64_t idx = static_cast<int64_t>(t) - 1;
-  for (;;) {
-    const int64_t mine = idx - lane;
-    uint64_t w = kFlagInc | P::to_word(P::kIdentity);  // before tile 0
-    if (mine >= 0) w = ld_relaxed_u64(&st[mine]);
-    bool done = false;
-    int take;
-    for (;;) {
-      take = window_take(__ballot_sync(0xffffffffu, (w & kFlagMask) != 0),
-                         __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagInc), &done);
-      if (take > 0) break;
-      const bool expired = __shfl_sync(0xffffffffu, globaltimer_ns() > deadline ? 1 : 0, 0) != 0;
-      if (expired) {
-        if (lane == 0) atomicOr(&misc->timeout, 1u);
-        done = true;
-        take = 0;
-        break;
-      }
-      __nanosleep(20);
-      if ((w & kFlagMask) == 0) w = ld_relaxed_u64(&st[mine]);
-    }
-    uint64_t v = lane < take ? P::from_word(w) : P::kIdentity;
+  int64_t base = static_cast<int64_t>(t) - 1;
+  bool done = false;
+  while (!done) {
+    uint64_t w[kLbRounds];
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint64_t o = __shfl_down_sync(0xffffffffu, v, off);
-      if (lane + off < 32) v = P::combine(o, v);  // o holds earlier tiles
+    for (int j = 0; j < kLbRounds; ++j) {
+      const int64_t mine = base - (32 * j + lane);
+      w[j] = mine >= 0 ? ld_relaxed_u64(&st[mine]) : (kFlagInc | P::to_word(P::kIdentity));
     }
-    v = __shfl_sync(0xffffffffu, v, 0);
-    acc = P::combine(v, acc);
-    if (done) break;
-    idx -= 32;
+#pragma unroll
+    for (int j = 0; j < kLbRounds; ++j) {
+      if (!done) {
+        const int64_t mine = base - (32 * j + lane);
+        int take;
+        for (;;) {
+          take = window_take(__ballot_sync(0xffffffffu, (w[j] & kFlagMask) != 0),
+                             __ballot_sync(0xffffffffu, (w[j] & kFlagMask) == kFlagInc), &done);
+          if (take > 0) break;
+          const bool expired = __shfl_sync(0xffffffffu, globaltimer_ns() > deadline ? 1 : 0, 0) != 0;
+          if (expired) {
+            if (lane == 0) atomicOr(&misc->timeout, 1u);
+            done = true;
+            take = 0;
+            break;
+          }
+          __nanosleep(20);
+          if ((w[j] & kFlagMask) == 0) w[j] = ld_relaxed_u64(&st[mine]);
+        }
+        uint64_t v = lane < take ? P::from_word(w[j]) : P::kIdentity;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint64_t o = __shfl_down_sync(0xffffffffu, v, off);
+          if (lane + off < 32) v = P::combine(o, v);  // o holds earlier tiles
+        }
+        v = __shfl_sync(0xffffffffu, v, 0);
+        acc = P::combine(v, acc);
+      }
+    }
+    base -= 32 * kLbRounds;
   }
   if (lane == 0) st_relaxed_u64(&st[t], kFlagInc | P::to_word(P::combine(acc, agg)));
+  return acc;
+}
+
+// Look-back over several independent additive chains at once (one status
+// word per tile and chain: flag | count).  Lanes are grouped by chain: with G
+// = ns rounded up to a power of two, lane l serves chain l % G and the
+// (l / G)-th predecessor of each sub-window, so every chain advances over
+// 32 / G predecessors per sub-window and kLbRounds sub-windows per round
+// trip.  Returns, in lane k < ns, the exclusive prefix of chain k.
+static __device__ int64_t lookback_sums(uint64_t* st, uint64_t t, uint32_t ns, const uint32_t* tile_tot,
+                                 uint64_t deadline, Misc* misc) {
+  const int lane = threadIdx.x & 31;
+  uint32_t G = 1;
+  while (G < ns) G <<= 1;
+  const int per = 32 / static_cast<int>(G);          // predecessors per sub-window
+  const uint32_t k = static_cast<uint32_t>(lane) & (G - 1);  // this lane's chain
+  const int i = lane / static_cast<int>(G);          // this lane's predecessor offset
+  uint32_t lanes_k = 0;                               // lanes serving chain k
+  for (int l = static_cast<int>(k); l < 32; l += static_cast<int>(G)) lanes_k |= 1u << l;
+  const bool active = k < ns;
+  if (lane < static_cast<int>(ns)) st_relaxed_u64(&st[t * ns + lane], (t == 0 ? kFlagInc : kFlagAgg) | tile_tot[lane]);
+  int64_t acc = 0;
+  if (t > 0) {
+    bool mydone = !active;  // this lane's chain found its inclusive prefix
+    int64_t base = static_cast<int64_t>(t) - 1;
+    while (__any_sync(0xffffffffu, !mydone)) {
+      uint64_t w[kLbRounds];
+#pragma unroll
+      for (int j = 0; j < kLbRounds; ++j) {
+        const int64_t mine = base - (per * j + i);
+        w[j] = (active && mine >= 0) ? ld_relaxed_u64(&st[mine * ns + k]) : kFlagInc;
+      }
+#pragma unroll
+      for (int j = 0; j < kLbRounds; ++j) {
+        const int64_t mine = base - (per * j + i);
+        int limit = -1;  // include lanes of chain k up to this lane index
+        bool done_now = false;
+        for (;;) {
+          const uint32_t valid = __ballot_sync(0xffffffffu, (w[j] & kFlagMask) != 0);
+          const uint32_t inc = __ballot_sync(0xffffffffu, (w[j] & kFlagMask) == kFlagInc);
+          const uint32_t bad = ~valid & lanes_k, incs = inc & lanes_k;
+          const int fi = bad ? __ffs(bad) - 1 : 32;
+          const int fc = incs ? __ffs(incs) - 1 : 32;
+          bool ready = true;
+          done_now = false;
+          if (mydone) {
+            limit = -1;
+          } else if (fc < fi) {
+            limit = fc;
+            done_now = true;
+          } else if (fi == 32) {
+            limit = 31;
+          } else {
+            ready = false;
+          }
+          if (__all_sync(0xffffffffu, ready)) break;
+          const bool expired = __shfl_sync(0xffffffffu, globaltimer_ns() > deadline ? 1 : 0, 0) != 0;
+          if (expired) {
+            if (lane == 0) atomicOr(&misc->timeout, 1u);
+            mydone = true;
+            limit = -1;
+            done_now = false;
+            break;
+          }
+          __nanosleep(20);
+          if ((w[j] & kFlagMask) == 0 && active && mine >= 0) w[j] = ld_relaxed_u64(&st[mine * ns + k]);
+        }
+        long long x = (!mydone && lane <= limit) ? static_cast<long long>(w[j] & ~kFlagMask) : 0ll;
+        for (int off = static_cast<int>(G); off < 32; off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        acc += x;
+        if (done_now) mydone = true;
+      }
+      base -= per * kLbRounds;
+    }
+  }
+  if (lane < static_cast<int>(ns))
+    st_relaxed_u64(&st[t * ns + lane], kFlagInc | static_cast<uint64_t>(acc + tile_tot[lane]));
   return acc;
 }
 
@@ -638,51 +729,11 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       __syncthreads();
       PP_PHASE(6);
 
-      // chain 3: per-slot byte counts, summed over the predecessors.  Each
-      // slot is its own single-word scan: flag | 48-bit count.
+      // chain 3: per-slot byte counts, summed over the predecessors; all
+      // slots advance together
       if (warp == 0) {
-        uint64_t* st3 = J.st_bytes + t * NS;
-        int64_t myacc = 0;  // lane k accumulates slot k
-        if (t > 0) {
-          if (lane < static_cast<int>(NS)) st_relaxed_u64(&st3[lane], kFlagAgg | H->tile_tot[lane]);
-          int64_t idx = static_cast<int64_t>(t) - 1;
-          uint32_t pending = (1u << NS) - 1u;  // slots without an inclusive prefix yet
-          while (pending) {
-            const int64_t mine = idx - lane;
-#pragma unroll 1
-            for (uint32_t k = 0; k < NS; ++k) {
-              if (!((pending >> k) & 1u)) continue;
-              uint64_t w = kFlagInc;  // before tile 0
-              if (mine >= 0) w = ld_relaxed_u64(&J.st_bytes[mine * NS + k]);
-              bool done = false;
-              int take;
-              for (;;) {
-                take = window_take(__ballot_sync(0xffffffffu, (w & kFlagMask) != 0),
-                                   __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagInc), &done);
-                if (take > 0) break;
-                const bool expired = __shfl_sync(0xffffffffu, globaltimer_ns() > deadline ? 1 : 0, 0) != 0;
-                if (expired) {
-                  if (lane == 0) atomicOr(&J.misc->timeout, 1u);
-                  done = true;
-                  take = 0;
-                  break;
-                }
-                __nanosleep(20);
-                if ((w & kFlagMask) == 0) w = ld_relaxed_u64(&J.st_bytes[mine * NS + k]);
-              }
-              long long x = lane < take ? static_cast<long long>(w & ~kFlagMask) : 0ll;
-#pragma unroll
-              for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-              if (lane == static_cast<int>(k)) myacc += x;
-              if (done) pending &= ~(1u << k);
-            }
-            idx -= 32;
-          }
-        }
-        if (lane < static_cast<int>(NS)) {
-          H->col_base[lane] = myacc;
-          st_relaxed_u64(&st3[lane], kFlagInc | static_cast<uint64_t>(myacc + H->tile_tot[lane]));
-        }
+        const int64_t base_k = lookback_sums(J.st_bytes, t, NS, H->tile_tot, deadline, J.misc);
+        if (lane < static_cast<int>(NS)) H->col_base[lane] = base_k;
         __syncwarp();
         if (lane == 0) {
           // staging regions share the destination's 16-byte phase so that
