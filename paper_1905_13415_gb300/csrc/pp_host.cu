@@ -153,6 +153,10 @@ ShapeInfo shape_for(int cfg) {
     case 6: return shape_info_m128x6();
     case 7: return shape_info_s128();
     case 8: return shape_info_mid3();
+    case 9: return shape_info_v48();
+    case 10: return shape_info_v64();
+    case 11: return shape_info_v32();
+    case 12: return shape_info_w48();
     default: return shape_info_mid();
   }
 }
@@ -319,11 +323,11 @@ using namespace pp;
 
 #ifdef PP_PHASE_TIMING
 // Profiling builds only (not part of include/parparaw.h): copies the
-// accumulated per-phase cycle totals of the tile kernel to out[0..9].
+// accumulated per-phase cycle totals of the tile kernel to out[0..15].
 extern "C" int parparaw_debug_phase_cycles(unsigned long long* out, int reset) {
   if (g_phase_cycles == nullptr) return -1;
   cudaDeviceSynchronize();
-  cudaMemcpy(out, g_phase_cycles, 10 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  cudaMemcpy(out, g_phase_cycles, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
   if (reset) cudaMemset(g_phase_cycles, 0, 16 * sizeof(unsigned long long));
   return 0;
 }
@@ -456,7 +460,7 @@ extern "C" pp_status parparaw_set_option(pp_parser* P, pp_option option, int64_t
   if (P == nullptr) return PP_E_ARG;
   switch (option) {
     case PP_OPT_TILE_CONFIG:
-      if (value < 0 || value > 8) return PP_E_ARG;
+      if (value < 0 || value > 12) return PP_E_ARG;
       P->tile_config = static_cast<int>(value);
       return PP_OK;
     case PP_OPT_TIMEOUT_MS:

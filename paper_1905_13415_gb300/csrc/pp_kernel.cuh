@@ -66,6 +66,7 @@ struct TileShape {
   static constexpr int MW = (B + 63) / 64; // 64-bit mask words per chunk
   static constexpr int NW = NT / 32;
   static constexpr int kStage = T + 32 * PP_MAX_STRING_COLUMNS + 64;
+  static_assert(T < 32768, "tile positions are 15-bit field-list entries");
 };
 
 struct SmemHead {
@@ -84,10 +85,19 @@ struct SmemHead {
   Tables tab;
   uint8_t str_col[PP_MAX_STRING_COLUMNS];  // slot -> column
   int32_t job_loaded;
-  uint32_t nconv;
   unsigned long long tile_last_rd;  // partial inputs: last record delimiter + 1
-  uint32_t conv_base, conv_cap;  // queue of numeric fields in the staging buffer's free tail
-  long long ph_cycles[10];  // profiling builds only
+  uint32_t eof_rd;                  // the input's last byte is a record delimiter
+  // field list of the current round (fields [f0, f0 + nwin) of the tile)
+  int32_t prev_pos;      // end of field f0 - 1 (the start of the tile's data - 1 for f0 = 0)
+  uint32_t rr0;          // record of field f0, relative to the tile's first record
+  uint32_t rr_last;      // record of the round's last field
+  int32_t next_prev_pos;
+  uint32_t rr_next;
+  uint32_t round_tot[PP_MAX_STRING_COLUMNS];   // string bytes of the round per slot
+  uint32_t round_base[PP_MAX_STRING_COLUMNS];  // string bytes of the earlier rounds
+#ifdef PP_PHASE_TIMING
+  long long ph_cycles[16];  // profiling builds only
+#endif
   Job jd;                  // the current job and its columns, staged from the
   Col cd[PP_MAX_COLUMNS];  // launch parameters / global memory once per job
 };
@@ -98,9 +108,24 @@ struct SmemLayout {
   static constexpr size_t kTile = kHead;
   static constexpr size_t kStage = kTile + ((Shape::T + 64 + 127) & ~size_t(127));
   static constexpr size_t kDm = kStage + ((Shape::kStage + 127) & ~size_t(127));
-  static constexpr size_t kDl = kDm + sizeof(uint64_t) * Shape::NT * Shape::MW;
-  static constexpr size_t kCnt = kDl + sizeof(uint64_t) * Shape::NT * Shape::MW;
-  static constexpr size_t kBytes = kCnt + sizeof(uint16_t) * Shape::NT * PP_MAX_STRING_COLUMNS;
+  static constexpr size_t kCnt = kDm + sizeof(uint64_t) * Shape::NT * Shape::MW;
+  static constexpr size_t kDex = kCnt + sizeof(uint16_t) * Shape::NT * PP_MAX_STRING_COLUMNS;
+  static constexpr size_t kFe = kDex + ((sizeof(uint16_t) * (Shape::NT + 1) + 15) & ~size_t(15));
+  // Field-list capacity: what an SM's shared memory (228 KB, 1 KB reserved
+  // per block) leaves at the shape's residency (at least 2 blocks), within
+  // [T/16, T/4] and at most 4960 entries of 8 bytes.  Tiles with more fields
+  // are processed in rounds.
+  static constexpr int kBlocks = Shape::MINB > 2 ? Shape::MINB : 2;
+  static constexpr long kPerBlock = 233472 / kBlocks - 1024;
+  static constexpr long kFit = (kPerBlock - static_cast<long>(kFe)) / 8;
+  static constexpr long kLo = kFit > Shape::T / 16 ? kFit : Shape::T / 16;
+  static constexpr long kHi = Shape::T / 4 < 4960 ? Shape::T / 4 : 4960;
+  static constexpr int kFcap = static_cast<int>(((kLo < kHi ? kLo : kHi) & ~31L) < 64 ? 64 : ((kLo < kHi ? kLo : kHi) & ~31L));
+  static constexpr size_t kFo = kFe + sizeof(uint32_t) * kFcap;
+  static constexpr size_t kRec = kFo + sizeof(uint16_t) * kFcap;
+  static constexpr size_t kBytes = kRec + sizeof(uint16_t) * kFcap;
+  // before the field list exists, its memory holds three chunk masks
+  static_assert(kBytes - kFe >= 3 * sizeof(uint64_t) * Shape::NT * Shape::MW, "field-list memory too small");
 };
 
 // ---------------------------------------------------- look-back (1 word) ---
@@ -368,6 +393,28 @@ __device__ __forceinline__ void smem_copy(uint8_t* dst, const uint8_t* src, int 
   while (n-- > 0) *dst++ = *src++;
 }
 
+// Warp-wide shared -> shared copy of n bytes (any alignments, no overlap):
+// aligned destination words assembled with funnel shifts, the ragged ends
+// byte by byte.  May read up to 4 bytes past the source end.
+__device__ __forceinline__ void warp_smem_copy(uint8_t* dst, const uint8_t* src, int n, int lane) {
+  const int head = min(n, static_cast<int>((4u - (reinterpret_cast<uintptr_t>(dst) & 3u)) & 3u));
+  if (lane < head) dst[lane] = src[lane];
+  dst += head;
+  src += head;
+  n -= head;
+  const int nw = n >> 2;
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  const uintptr_t sa = reinterpret_cast<uintptr_t>(src);
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(sa & ~uintptr_t(3));
+  const uint32_t sh = static_cast<uint32_t>(sa & 3u) * 8u;
+  for (int k = lane; k < nw; k += 32) d[k] = __funnelshift_r(s[k], s[k + 1], sh);
+  if (lane < (n & 3)) dst[4 * nw + lane] = src[4 * nw + lane];
+}
+
+// String fields with more data bytes in a tile than this are copied by a
+// whole warp.
+constexpr uint32_t kLongField = 40;
+
 __device__ __forceinline__ void store_value(const Col& col, uint32_t type, uint64_t r, uint64_t v) {
   if (type == PP_INT32 || type == PP_DATE_D)
     static_cast<uint32_t*>(col.values)[r] = static_cast<uint32_t>(v);
@@ -386,8 +433,11 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
   uint8_t* s_tile = smem + Lay::kTile;
   uint8_t* s_stage = smem + Lay::kStage;
   uint64_t* s_dm = reinterpret_cast<uint64_t*>(smem + Lay::kDm);
-  uint64_t* s_dl = reinterpret_cast<uint64_t*>(smem + Lay::kDl);
   uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + Lay::kCnt);
+  uint16_t* s_dex = reinterpret_cast<uint16_t*>(smem + Lay::kDex);  // data bytes before each chunk
+  uint32_t* s_fe = reinterpret_cast<uint32_t*>(smem + Lay::kFe);    // field list (one round)
+  uint16_t* s_fo = reinterpret_cast<uint16_t*>(smem + Lay::kFo);
+  uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem + Lay::kRec);
   const Tables& TB = H->tab;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -401,7 +451,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
   uint32_t phase = 0;
 #ifdef PP_PHASE_TIMING
   if (tid == 0)
-    for (int k = 0; k < 10; ++k) H->ph_cycles[k] = 0;
+    for (int k = 0; k < 16; ++k) H->ph_cycles[k] = 0;
   long long ph_last = clock64();
 #endif
 
@@ -420,10 +470,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       }
       H->item = item;
       H->job = j;
-      H->nconv = 0;
       H->tile_last_rd = 0;
-      H->conv_base = 0;  // no string bytes staged: the whole buffer is free
-      H->conv_cap = static_cast<uint32_t>(Shape::kStage) / 6u;
+      H->eof_rd = 0;
     }
     __syncthreads();
     const unsigned long long item = H->item;
@@ -543,6 +591,9 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       for (int w = 0; w < MW; ++w) spec[w] &= bit_range(lo - 64 * w, hi - 64 * w);
     }
 
+    const int P0 = static_cast<int>(min(max(static_cast<int64_t>(J.head) - static_cast<int64_t>(v0), int64_t(0)),
+                                        static_cast<int64_t>(T)));
+    const int PE = static_cast<int>(v1 - v0);  // end of the tile's bytes
     // ------------------------------------ a2: multi-state simulation
     uint64_t vec = kIdentityVec;
     {
@@ -581,7 +632,6 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       dm[w] = bit_range(lo - 64 * w, hi - 64 * w) & ~spec[w];  // runs are data unless fixed below
       fm[w] = rm[w] = 0;
     }
-    uint32_t s_end;
     {
       const uint32_t inv = TB.invalid_state;
       const uint32_t ca = TB.catch_all;
@@ -628,34 +678,47 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         const int rs = max(prev + 1, lo);
         if (rs < hi) run(rs, hi);
       }
-      s_end = s;
       if (inv_pos >= 0)
         atomicMin(&J.misc->first_invalid,
                   static_cast<unsigned long long>(cv0 + inv_pos - static_cast<int64_t>(J.head)));
     }
 #pragma unroll
-    for (int w = 0; w < MW; ++w) {
-      s_dm[tid * MW + w] = dm[w];
-      s_dl[tid * MW + w] = fm[w] | rm[w];
-    }
+    for (int w = 0; w < MW; ++w) s_dm[tid * MW + w] = dm[w];
 
     // ---------------------------------- a5: records, columns + chain 2
-    uint32_t nrec = 0, ncol = 0;
+    // Per chunk: records, column offset (abs/rel), data bytes and
+    // delimiters; one block scan carries all four (records and columns with
+    // the (+, oplus) pair, data bytes and delimiters as plain sums).
+    uint32_t nrec = 0, ncol = 0, ndl = 0, ndat = 0;
     {
       int last_rd = -1;
 #pragma unroll
       for (int w = 0; w < MW; ++w) {
         nrec += __popcll(rm[w]);
+        ndl += __popcll(fm[w] | rm[w]);
+        ndat += __popcll(dm[w]);
         if (rm[w]) last_rd = 64 * w + 63 - __clzll(static_cast<long long>(rm[w]));
       }
 #pragma unroll
       for (int w = 0; w < MW; ++w) ncol += __popcll(fm[w] & ~bits_below(last_rd + 1 - 64 * w));
       if (TB.partial && last_rd >= 0)
         atomicMax(&H->tile_last_rd, static_cast<unsigned long long>(cv0 + last_rd + 1 - static_cast<int64_t>(J.head)));
+      if (lo < hi && cv0 + hi == static_cast<int64_t>(VL) && test_bit(rm, hi - 1)) H->eof_rd = 1u;
     }
-    uint32_t rc_tile;
-    const uint32_t rc_ex = block_exclusive_scan<NT>(rc_pack(nrec, ncol, nrec > 0), rc_combine,
-                                                    rc_pack(0, 0, false), H->wsum32, &rc_tile);
+    uint64_t sc_tile;
+    const uint64_t sc_ex = block_exclusive_scan<NT>(
+        static_cast<uint64_t>(rc_pack(nrec, ncol, nrec > 0)) | (static_cast<uint64_t>(ndat | (ndl << 16)) << 32),
+        [](uint64_t a, uint64_t b) {
+          return static_cast<uint64_t>(rc_combine(static_cast<uint32_t>(a), static_cast<uint32_t>(b))) |
+                 (((a >> 32) + (b >> 32)) << 32);
+        },
+        uint64_t(0), H->wsum64, &sc_tile);
+    const uint32_t rc_ex = static_cast<uint32_t>(sc_ex), rc_tile = static_cast<uint32_t>(sc_tile);
+    const uint32_t dat_ex = static_cast<uint32_t>(sc_ex >> 32) & 0xFFFFu;
+    const uint32_t dl_ex = static_cast<uint32_t>(sc_ex >> 48);
+    const uint32_t ND = static_cast<uint32_t>(sc_tile >> 48);  // delimiters of the tile
+    s_dex[tid] = static_cast<uint16_t>(dat_ex);
+    if (tid == NT - 1) s_dex[NT] = static_cast<uint16_t>((sc_tile >> 32) & 0xFFFFu);
     PP_PHASE(4);
     if (TB.partial && tid == 0 && H->tile_last_rd)  // after the scan's barriers
       atomicMax(&J.misc->last_record_end, H->tile_last_rd);
@@ -668,30 +731,110 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     PP_PHASE(5);
     const uint64_t tile_row0 = H->prefix_rc & kRecMask;
     const uint32_t tile_col0 = static_cast<uint32_t>((H->prefix_rc >> 40) & 0x1FFFFF);
-    const uint64_t row_start = tile_row0 + (rc_ex & 0xFFFFu);
+    const uint32_t row_start = rc_ex & 0xFFFFu;  // relative to the tile's first record
     const uint32_t col_start = (rc_ex >> 31) ? ((rc_ex >> 16) & kColSat)
                                              : min(tile_col0 + ((rc_ex >> 16) & kColSat), kColSat);
+    // the tile's open field (after its last delimiter): record and column
+    const uint32_t rec_tile = rc_tile & 0xFFFFu;
+    const uint32_t col_end = (rc_tile >> 31) ? ((rc_tile >> 16) & kColSat)
+                                             : min(tile_col0 + ((rc_tile >> 16) & kColSat), kColSat);
 
     const uint32_t C = TB.num_columns;
     const uint32_t NS = TB.num_str;
-    // ------------------------------- string bytes per column + chain 3
-    if (NS > 0) {
-      for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
-      uint32_t c = col_start;
-      int pos = lo;
-      uint64_t dl[MW];
-#pragma unroll
-      for (int w = 0; w < MW; ++w) dl[w] = fm[w] | rm[w];
-      BitIter<MW> it(dl);
-      for (;;) {
-        const int d = it.next();
-        const int e = d >= 0 ? d : hi;
-        if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += popc_range(dm, pos, e);
-        if (d < 0) break;
-        c = test_bit(rm, d) ? 0u : min(c + 1, kColSat);
-        pos = d + 1;
-      }
+    const bool last_tile = (t + 1 == J.ntiles);
+    const uint64_t rows_cap = J.rows_cap;
+    // The field after the last delimiter ends at the input's end when the
+    // input ends here.  If the input's last byte is a record delimiter that
+    // field does not exist; otherwise it closes a trailing record when the
+    // final state accepts (and the input is whole).
+    const bool open_dead = last_tile && H->eof_rd;
+    const bool trailing =
+        last_tile && !TB.partial && !H->eof_rd && ((TB.accept_mask >> tile_send) & 1u) && PE > P0;
+    const uint32_t NF = ND + 1;  // fields of the tile, the open one included
+    constexpr uint32_t FCAP = static_cast<uint32_t>(Lay::kFcap);
+    const uint32_t nrounds = (NF + FCAP - 1) / FCAP;
 
+    // Data bytes of the tile before tile position p (p in [0, T]).
+    auto data_before = [&](int p) -> uint32_t {
+      const int u = p / B;
+      const int off = p - u * B;
+      uint32_t n = s_dex[u];
+      if (off > 0) {
+#pragma unroll
+        for (int w = 0; w < MW; ++w) n += __popcll(s_dm[u * MW + w] & bits_below(off - 64 * w));
+      }
+      return n;
+    };
+
+    // First data position in [p, e), else e.  Mask bits at or past B are
+    // never set.
+    auto first_data = [&](int p, int e) -> int {
+      while (p < e) {
+        const int u = p / B, i = p - u * B;
+        const uint64_t w = s_dm[u * MW + (i >> 6)] & ~bits_below(i & 63);
+        if (w) return min(u * B + (i & ~63) + __ffsll(static_cast<long long>(w)) - 1, e);
+        p = (i & ~63) + 64 >= B ? (u + 1) * B : u * B + (i & ~63) + 64;
+      }
+      return e;
+    };
+
+    // Field list of one round: entry i describes field f0 + i of the tile,
+    // [15:0) its end position (a delimiter, or PE for the open field),
+    // [15] it ends a record, [23:16] its column (saturated), [24] open field.
+    // s_rec[k] = first entry of the round's k-th record.  The thread that
+    // writes the round's last entry leaves the next round's starting point.
+    auto build_round = [&](uint32_t f0, uint32_t f1) {
+      const uint32_t rr0 = H->rr0;
+      if (tid == 0) s_rec[0] = 0;
+      if (dl_ex < f1 && dl_ex + ndl > f0) {
+        uint32_t g = dl_ex, c = col_start, rr = row_start;
+        uint64_t dl[MW];
+#pragma unroll
+        for (int w = 0; w < MW; ++w) dl[w] = fm[w] | rm[w];
+        BitIter<MW> it(dl);
+        for (int d = it.next(); d >= 0 && g < f1; d = it.next(), ++g) {
+          const bool rd = test_bit(rm, d);
+          if (g >= f0) {
+            const int pos = tid * B + d;
+            s_fe[g - f0] = static_cast<uint32_t>(pos) | (rd ? 0x8000u : 0u) | (min(c, 255u) << 16);
+            if (rd && g + 1 < f1) s_rec[rr + 1 - rr0] = static_cast<uint16_t>(g + 1 - f0);
+            if (g + 1 == f1) {
+              H->rr_last = rr;
+              H->rr_next = rr + (rd ? 1u : 0u);
+              H->next_prev_pos = pos;
+            }
+          }
+          if (rd) {
+            ++rr;
+            c = 0;
+          } else {
+            c = min(c + 1, kColSat);
+          }
+        }
+      }
+      if (tid == NT - 1 && ND >= f0 && ND < f1) {
+        s_fe[ND - f0] = static_cast<uint32_t>(PE) | (trailing ? 0x8000u : 0u) | (min(col_end, 255u) << 16) |
+                        0x1000000u;
+        H->rr_last = rec_tile;
+      }
+      __syncthreads();
+    };
+
+    // Per-slot string bytes of the round's fields; each thread takes an
+    // equal share of consecutive entries.  Leaves the exclusive per-thread
+    // sums in s_cnt and the round totals in round_tot.
+    auto count_round = [&](uint32_t nwin) {
+      const uint32_t per = (nwin + NT - 1) / NT;
+      const uint32_t b0 = min(tid * per, nwin), b1 = min(b0 + per, nwin);
+      for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
+      uint32_t dprev = data_before(b0 == 0 ? H->prev_pos + 1 : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu));
+      for (uint32_t g = b0; g < b1; ++g) {
+        const uint32_t fe = s_fe[g];
+        const uint32_t de = data_before(static_cast<int>(fe & 0x7FFFu));
+        const uint32_t c = (fe >> 16) & 0xFFu;
+        if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(de - dprev);
+        dprev = de;
+      }
       // block scan of the per-slot counts, two 16-bit slots per word
       const uint32_t K = (NS + 1) / 2;
       uint32_t incl[PP_MAX_STRING_COLUMNS / 2], own[PP_MAX_STRING_COLUMNS / 2];
@@ -721,14 +864,46 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           if (2 * k + 1 < static_cast<int>(NS)) s_cnt[(2 * k + 1) * NT + tid] = static_cast<uint16_t>(ex >> 16);
           if (tid == 0) {
             const uint32_t tot = H->wsumk[k][Shape::NW - 1];
-            H->tile_tot[2 * k] = tot & 0xFFFFu;
-            if (2 * k + 1 < static_cast<int>(NS)) H->tile_tot[2 * k + 1] = tot >> 16;
+            H->round_tot[2 * k] = tot & 0xFFFFu;
+            if (2 * k + 1 < static_cast<int>(NS)) H->round_tot[2 * k + 1] = tot >> 16;
           }
         }
       }
-      __syncthreads();
-      PP_PHASE(6);
+      // each thread reads back only its own sums; round_tot is written by
+      // thread 0 and read by warp 0
+      __syncwarp();
+    };
 
+    auto start_rounds = [&]() {
+      if (tid == 0) {
+        H->prev_pos = P0 - 1;
+        H->rr0 = 0;
+      }
+      if (tid < PP_MAX_STRING_COLUMNS) H->round_base[tid] = 0;
+      __syncthreads();
+    };
+    auto next_round = [&]() {  // after a barrier that follows the round's last use of its list
+      if (tid == 0) {
+        H->prev_pos = H->next_prev_pos;
+        H->rr0 = H->rr_next;
+      }
+      if (tid < static_cast<int>(NS)) H->round_base[tid] += H->round_tot[tid];
+      __syncthreads();
+    };
+
+    // ------------------------ pass 1: string bytes per column + chain 3
+    if (NS > 0) {
+      start_rounds();
+      for (uint32_t r = 0; r < nrounds; ++r) {
+        const uint32_t f0 = r * FCAP, f1 = min(f0 + FCAP, NF);
+        build_round(f0, f1);
+        PP_PHASE(13);
+        count_round(f1 - f0);
+        if (r + 1 < nrounds) next_round();
+      }
+      if (tid < static_cast<int>(NS)) H->tile_tot[tid] = H->round_base[tid] + H->round_tot[tid];
+      __syncwarp();  // written and read by warp 0 (NS <= 32)
+      PP_PHASE(6);
       // chain 3: per-slot byte counts, summed over the predecessors; all
       // slots advance together
       if (warp == 0) {
@@ -745,71 +920,29 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
             H->stage_off[k] = off;
             off += H->tile_tot[k];
           }
-          H->conv_base = (off + 3u) & ~3u;
-          H->conv_cap = (static_cast<uint32_t>(Shape::kStage) - H->conv_base) / 6u;
         }
       }
       __syncthreads();
       PP_PHASE(7);
     }
 
-    // ----------------- a6 / a7 / a8: gather, offsets, conversion, rejects
-    const bool last_tile = (t + 1 == J.ntiles);
-    const uint64_t rows_cap = J.rows_cap;
-    auto record_end = [&](uint64_t r, uint32_t nfields) {
-      if (r >= rows_cap) return;
-      if (nfields != C) atomicOr(&J.fail_bits[r >> 5], 1u << (r & 31));
-      for (uint32_t c2 = nfields; c2 < C; ++c2) {  // fields the record lacks
-        const uint32_t slot = TB.str_slot[c2];
-        if (slot != 0xFF)
-          cols[c2].offsets[r + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
-        else
-          store_value(cols[c2], TB.col_type[c2], r, 0);
-      }
-    };
-    // Converts the numeric field (r, c) that starts at tile position p0.  The
-    // common case -- the field ends inside the tile and its data bytes are
-    // contiguous -- parses straight from shared memory; otherwise the data
-    // bytes are gathered first (through the tile's masks, then from global
-    // memory past the tile, re-simulating from the tile's end state).
-    auto convert_at = [&](uint64_t r, uint32_t c, int p0) {
+    // ----------------- a6 / a7 / a8: offsets, gather, conversion, rejects
+    // Converts numeric field (r, c) occupying tile positions [a, e); `ended`:
+    // the field ends there (else it continues past the tile, and its data
+    // bytes are gathered from global memory by re-simulating from the
+    // tile's end state).
+    auto convert_field = [&](uint64_t r, uint32_t c, int a, int e, bool ended) {
       const uint32_t type = TB.col_type[c];
-      const int tend = static_cast<int>(v1 - v0);
-      int first = -1, last = -1, n = 0;
-      bool ended = false;
-      int x = p0;
-      while (x < tend) {
-        const int u = x / B, i = x - u * B;
-        const int span = min(min(64 - (i & 63), B - i), tend - x);
-        const uint64_t dlw = s_dl[u * MW + (i >> 6)] >> (i & 63);
-        const uint64_t dmw = s_dm[u * MW + (i >> 6)] >> (i & 63);
-        const int dpos = dlw ? __ffsll(static_cast<long long>(dlw)) - 1 : 64;
-        const uint64_t bits = dmw & bits_below(min(dpos, span));
-        if (bits) {
-          if (first < 0) first = x + __ffsll(static_cast<long long>(bits)) - 1;
-          last = x + 63 - __clzll(static_cast<long long>(bits));
-          n += __popcll(bits);
-        }
-        if (dpos < span) {
-          ended = true;
-          break;
-        }
-        x += span;
-        if (n > kNumericMaxLen) break;
-      }
-      if (!ended && x >= tend && v1 >= VL) ended = true;  // the input ends the field
       uint64_t val = 0;
       int st;
-      if (n > kNumericMaxLen) {
-        st = kConvFail;
-      } else if (ended && (n == 0 || last - first + 1 == n)) {
-        st = convert_value(type, s_tile + (n ? first : 0), n, &val);
+      const int n_in = static_cast<int>(data_before(e) - data_before(a));
+      if (ended && n_in == e - a) {
+        st = n_in > kNumericMaxLen ? kConvFail : convert_value(type, s_tile + a, n_in, &val);
       } else {
         uint8_t buf[kNumericMaxLen + 1];
         int m = 0;
-        for (int y = p0; y < tend && m <= kNumericMaxLen; ++y) {
+        for (int y = a; y < e && m <= kNumericMaxLen; ++y) {
           const int u = y / B, i = y - u * B;
-          if ((s_dl[u * MW + (i >> 6)] >> (i & 63)) & 1ull) break;
           if ((s_dm[u * MW + (i >> 6)] >> (i & 63)) & 1ull) buf[m++] = s_tile[y];
         }
         if (!ended && m <= kNumericMaxLen) {
@@ -837,107 +970,167 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         if (st == kConvFail) atomicOr(&J.fail_bits[r >> 5], bit);
       }
     };
-    auto stage_piece = [&](uint32_t slot, int a, int b) {
-      if (a >= b) return;
-      if (popc_range(dm, a, b) == b - a) {  // all data: one copy (text fields)
-        const uint32_t at = H->stage_off[slot] + s_cnt[slot * NT + tid];
-        smem_copy(s_stage + at, chunk + a, b - a);
-        s_cnt[slot * NT + tid] = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (b - a));
-        return;
-      }
-      int x = a;
-      while (x < b) {
-        const int rs = next_bit(dm, x, b, true);
-        if (rs >= b) break;
-        const int re = next_bit(dm, rs, b, false);
-        const uint32_t at = H->stage_off[slot] + s_cnt[slot * NT + tid];
-        smem_copy(s_stage + at, chunk + rs, re - rs);
-        s_cnt[slot * NT + tid] = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (re - rs));
-        x = re;
-      }
-    };
 
-    {
-      // Walk the chunk's delimiters once.  Each event ends the current field
-      // piece (its string bytes are staged), a delimiter also ends the field
-      // (offset, record end) and opens the next one (converted here if
-      // numeric).  The end of the input closes the trailing record.
-      uint32_t c = col_start;
-      uint64_t r = row_start;
-      int pos = lo;
-      const bool eof_here = last_tile && lo < hi && cv0 + hi == static_cast<int64_t>(VL);
-      bool trailing = eof_here && !TB.partial && !test_bit(rm, hi - 1) && ((TB.accept_mask >> s_end) & 1u);
-      bool opens = t == 0 && tid == 0 && J.len > 0;  // the input's first field
-      uint64_t dl[MW];
-#pragma unroll
-      for (int w = 0; w < MW; ++w) dl[w] = fm[w] | rm[w];
-      BitIter<MW> it(dl);
-      for (;;) {
-        if (opens && c < C && TB.num_slot[c] != 0xFF && r < rows_cap) {
-          const uint32_t slot_i = atomicAdd(&H->nconv, 1u);
-          if (slot_i < H->conv_cap) {
-            uint32_t* qa = reinterpret_cast<uint32_t*>(s_stage + H->conv_base);  // start | column << 16
-            uint16_t* qb = reinterpret_cast<uint16_t*>(qa + H->conv_cap);        // row - first row of tile
-            qa[slot_i] = static_cast<uint32_t>(tid * B + pos) | (c << 16);
-            qb[slot_i] = static_cast<uint16_t>(r - tile_row0);
-          } else {
-            convert_at(r, c, tid * B + pos);
+    // ------------------------------------------- pass 2: emit, by rounds
+    if (NS == 0 || nrounds > 1) start_rounds();  // else pass 1's only round is still in place
+    for (uint32_t r = 0; r < nrounds; ++r) {
+      const uint32_t f0 = r * FCAP, f1 = min(f0 + FCAP, NF), nwin = f1 - f0;
+      if (NS == 0 || nrounds > 1) {
+        build_round(f0, f1);
+        if (NS > 0) count_round(nwin);
+        PP_PHASE(14);
+      }
+      const uint32_t rr0 = H->rr0;
+      const uint32_t nrec_win = H->rr_last - rr0 + 1;
+      const int prev_pos = H->prev_pos;
+
+      // (1) equal shares of consecutive entries: per-slot running byte
+      // positions -> s_fo (field end minus data bytes before it, mod 2^16),
+      // and records with a wrong field count (rare)
+      {
+        const uint32_t per = (nwin + NT - 1) / NT;
+        const uint32_t b0 = min(tid * per, nwin), b1 = min(b0 + per, nwin);
+        for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = static_cast<uint16_t>(s_cnt[k * NT + tid] + H->round_base[k]);
+        uint32_t dprev = data_before(b0 == 0 ? prev_pos + 1 : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu));
+        for (uint32_t g = b0; g < b1; ++g) {
+          const uint32_t fe = s_fe[g];
+          const int e = static_cast<int>(fe & 0x7FFFu);
+          const uint32_t c = (fe >> 16) & 0xFFu;
+          if (NS > 0) {
+            const uint32_t de = data_before(e);
+            if (c < C && TB.str_slot[c] != 0xFF) {
+              const uint32_t slot = TB.str_slot[c];
+              const uint16_t run = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (de - dprev));
+              s_cnt[slot * NT + tid] = run;
+              s_fo[g] = static_cast<uint16_t>(run - de);
+            }
+            dprev = de;
+          }
+          if ((fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
+            // the record ends with the wrong number of fields: reject it and
+            // give the missing columns their defaults
+            uint32_t klo = 0, khi = nrec_win - 1;
+            while (klo < khi) {
+              const uint32_t mid = (klo + khi + 1) >> 1;
+              if (s_rec[mid] <= g) klo = mid; else khi = mid - 1;
+            }
+            const uint64_t row = tile_row0 + rr0 + klo;
+            if (row < rows_cap) {
+              atomicOr(&J.fail_bits[row >> 5], 1u << (row & 31));
+              for (uint32_t c2 = c + 1; c2 < C; ++c2) {
+                const uint32_t slot = TB.str_slot[c2];
+                if (slot != 0xFF)
+                  cols[c2].offsets[row + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
+                else
+                  store_value(cols[c2], TB.col_type[c2], row, 0);
+              }
+            }
           }
         }
-        const int d = it.next();
-        int e;
-        bool is_rd = false, ends_field = true;
-        if (d >= 0) {
-          e = d;
-          is_rd = test_bit(rm, d);
-        } else if (trailing) {
-          e = hi;
-          is_rd = true;
-          trailing = false;
-        } else {
-          e = hi;
-          ends_field = false;
-        }
-        const uint32_t slot = c < C ? TB.str_slot[c] : 0xFFu;
-        if (slot != 0xFF) {
-          stage_piece(slot, pos, e);
-          if (ends_field && r < rows_cap) cols[c].offsets[r + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
-        }
-        if (!ends_field) break;
-        if (is_rd) {
-          record_end(r, c + 1 > kColSat ? kColSat : c + 1);
-          ++r;
-          c = 0;
-        } else {
-          c = min(c + 1, kColSat);
-        }
-        pos = e + 1;
-        opens = d >= 0 && !(is_rd && (cv0 + e + 1) >= static_cast<int64_t>(VL));
-        if (d < 0) break;
       }
-      if (eof_here) {
-        J.misc->rows = static_cast<int64_t>(r);  // read by the finalize kernel only
-        J.misc->final_state = static_cast<int32_t>(s_end);
-        for (uint32_t k = 0; k < NS; ++k) J.misc->bytes_total[k] = H->col_base[k] + H->tile_tot[k];
-        J.misc->done = 1u;
-      }
-    }
+      __syncthreads();
+      PP_PHASE(10);
 
-    // --------------------- a7: queued numeric fields, one per thread
-    __syncthreads();
-    {
-      const uint32_t nq = min(H->nconv, H->conv_cap);
-      const uint32_t* qa = reinterpret_cast<const uint32_t*>(s_stage + H->conv_base);
-      const uint16_t* qb = reinterpret_cast<const uint16_t*>(qa + H->conv_cap);
-      for (uint32_t i = tid; i < nq; i += NT) {
-        const uint32_t a = qa[i];
-        convert_at(tile_row0 + qb[i], a >> 16, static_cast<int>(a & 0xFFFFu));
+      // (2) string offsets and numeric conversions, record by record: G
+      // threads per record take every G-th field (G = 1 when records are
+      // at least as many as threads: lanes of a warp then take consecutive
+      // records column by column)
+      const uint32_t G = max(1u, min(C, static_cast<uint32_t>(NT) / nrec_win));
+      for (uint32_t j = tid; j < nrec_win * G; j += NT) {
+        const uint32_t k = j / G, sub = j - k * G;
+        const uint64_t row = tile_row0 + rr0 + k;
+        if (row >= rows_cap) break;
+        const uint32_t gb = s_rec[k], ge = k + 1 < nrec_win ? s_rec[k + 1] : nwin;
+        for (uint32_t g = gb + sub; g < ge; g += G) {
+          const uint32_t fe = s_fe[g];
+          const uint32_t c = (fe >> 16) & 0xFFu;
+          const bool open = (fe >> 24) & 1u;
+          if (c >= C || (open && open_dead)) break;
+          const int e = static_cast<int>(fe & 0x7FFFu);
+          const uint32_t slot = TB.str_slot[c];
+          if (slot != 0xFF) {
+            if (!open || (fe & 0x8000u))
+              cols[c].offsets[row + 1] =
+                  H->col_base[slot] + static_cast<uint16_t>(s_fo[g] + data_before(e));
+          } else if (TB.num_slot[c] != 0xFF && (f0 + g > 0 || t == 0)) {
+            const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & 0x7FFFu) + 1 : (f0 == 0 ? P0 : prev_pos + 1);
+            convert_field(row, c, a, e, !open || last_tile);
+          }
+        }
       }
+
+      PP_PHASE(11);
+      // (3) string fields into their per-column staging regions: a warp
+      // takes 32 consecutive fields at a time; each lane copies its field if
+      // short, then the warp copies the long ones together, one by one
+      if (NS > 0) {
+        for (uint32_t base = warp * 32; base < nwin; base += NT) {
+          const uint32_t g = base + lane;
+          bool is_long = false;
+          int fd = 0;
+          uint32_t nb = 0, doff = 0;
+          bool contiguous = true;
+          if (g < nwin) {
+            const uint32_t fe = s_fe[g];
+            const uint32_t c = (fe >> 16) & 0xFFu;
+            if (c < C && TB.str_slot[c] != 0xFF && !(((fe >> 24) & 1u) && open_dead)) {
+              const int e = static_cast<int>(fe & 0x7FFFu);
+              const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & 0x7FFFu) + 1 : prev_pos + 1;
+              const uint32_t da = data_before(a);
+              nb = data_before(e) - da;
+              if (nb > 0) {
+                doff = H->stage_off[TB.str_slot[c]] + static_cast<uint16_t>(s_fo[g] + da);
+                fd = first_data(a, e);
+                contiguous = data_before(fd + static_cast<int>(nb)) == da + nb;
+                if (nb > kLongField) {
+                  is_long = true;
+                } else if (contiguous) {
+                  smem_copy(s_stage + doff, s_tile + fd, static_cast<int>(nb));
+                } else {
+                  uint8_t* dst = s_stage + doff;
+                  for (int x = fd; x < e; ++x)
+                    if ((s_dm[(x / B) * MW + ((x % B) >> 6)] >> ((x % B) & 63)) & 1ull) *dst++ = s_tile[x];
+                }
+              }
+            }
+          }
+          uint32_t longs = __ballot_sync(0xffffffffu, is_long);
+          while (longs) {
+            const int src = __ffs(static_cast<int>(longs)) - 1;
+            longs &= longs - 1;
+            const int lfd = __shfl_sync(0xffffffffu, fd, src);
+            const int lnb = static_cast<int>(__shfl_sync(0xffffffffu, nb, src));
+            const uint32_t ldoff = __shfl_sync(0xffffffffu, doff, src);
+            if (__shfl_sync(0xffffffffu, contiguous, src)) {
+              warp_smem_copy(s_stage + ldoff, s_tile + lfd, lnb, lane);
+            } else {  // data bytes with gaps: each lane places the bytes it holds by their rank
+              const uint32_t lfe = s_fe[base + src];
+              const int e = static_cast<int>(lfe & 0x7FFFu);
+              const uint32_t d0 = data_before(lfd);
+              for (int u = lfd / B; u * B < e; ++u) {
+                for (int x = u * B + lane; x < (u + 1) * B; x += 32) {
+                  if (x < lfd || x >= e) continue;
+                  const int i = x - u * B;
+                  if ((s_dm[u * MW + (i >> 6)] >> (i & 63)) & 1ull) s_stage[ldoff + (data_before(x) - d0)] = s_tile[x];
+                }
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+      PP_PHASE(12);
+      if (r + 1 < nrounds) next_round();
+    }
+    if (last_tile && tid == 0) {
+      J.misc->rows = static_cast<int64_t>(tile_row0 + rec_tile + (trailing ? 1u : 0u));  // read by the finalize kernel only
+      J.misc->final_state = static_cast<int32_t>(tile_send);
+      for (uint32_t k = 0; k < NS; ++k) J.misc->bytes_total[k] = H->col_base[k] + H->tile_tot[k];
+      J.misc->done = 1u;
     }
 
     // ------------------- write the gathered string bytes, 16 B per thread
     if (NS > 0) {
-      __syncthreads();
       PP_PHASE(8);
       for (uint32_t k = 0; k < NS; ++k) {
         const Col& col = cols[H->str_col[k]];
@@ -965,7 +1158,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
   }
 #ifdef PP_PHASE_TIMING
   if (tid == 0 && L.phase_cycles != nullptr)
-    for (int k = 0; k < 10; ++k) atomicAdd(&L.phase_cycles[k], static_cast<unsigned long long>(H->ph_cycles[k]));
+    for (int k = 0; k < 16; ++k) atomicAdd(&L.phase_cycles[k], static_cast<unsigned long long>(H->ph_cycles[k]));
 #endif
 }
 
