@@ -65,7 +65,6 @@ struct TileShape {
   static constexpr int T = NT * B;         // bytes per tile
   static constexpr int MW = (B + 63) / 64; // 64-bit mask words per chunk
   static constexpr int NW = NT / 32;
-  static constexpr int kStage = T + 32 * PP_MAX_STRING_COLUMNS + 64;
   static_assert(T < 32768, "tile positions are 15-bit field-list entries");
 };
 
@@ -78,7 +77,6 @@ struct SmemHead {
   uint64_t prefix_rc;    // chain 2 exclusive prefix of this tile
   int64_t col_base[PP_MAX_STRING_COLUMNS];   // chain 3 exclusive prefix
   uint32_t tile_tot[PP_MAX_STRING_COLUMNS];
-  uint32_t stage_off[PP_MAX_STRING_COLUMNS];
   uint64_t wsum64[32];
   uint32_t wsum32[32];
   uint32_t wsumk[PP_MAX_STRING_COLUMNS / 2][32];
@@ -106,8 +104,7 @@ template <class Shape>
 struct SmemLayout {
   static constexpr size_t kHead = (sizeof(SmemHead) + 127) & ~size_t(127);
   static constexpr size_t kTile = kHead;
-  static constexpr size_t kStage = kTile + ((Shape::T + 64 + 127) & ~size_t(127));
-  static constexpr size_t kDm = kStage + ((Shape::kStage + 127) & ~size_t(127));
+  static constexpr size_t kDm = kTile + ((Shape::T + 64 + 127) & ~size_t(127));
   static constexpr size_t kCnt = kDm + sizeof(uint64_t) * Shape::NT * Shape::MW;
   static constexpr size_t kDex = kCnt + sizeof(uint16_t) * Shape::NT * PP_MAX_STRING_COLUMNS;
   static constexpr size_t kFe = kDex + ((sizeof(uint16_t) * (Shape::NT + 1) + 15) & ~size_t(15));
@@ -358,7 +355,7 @@ struct BitIter {
   }
 };
 
-// shared -> shared byte copy: bytes up to a 4-byte aligned destination, then
+// shared -> shared or global byte copy: bytes up to a 4-byte aligned destination, then
 // 32-bit words assembled with funnel shifts, four per step (the source loads
 // of a step are independent).  May read up to 20 bytes past the source end.
 __device__ __forceinline__ void smem_copy(uint8_t* dst, const uint8_t* src, int n) {
@@ -393,22 +390,27 @@ __device__ __forceinline__ void smem_copy(uint8_t* dst, const uint8_t* src, int 
   while (n-- > 0) *dst++ = *src++;
 }
 
-// Warp-wide shared -> shared copy of n bytes (any alignments, no overlap):
-// aligned destination words assembled with funnel shifts, the ragged ends
-// byte by byte.  May read up to 4 bytes past the source end.
-__device__ __forceinline__ void warp_smem_copy(uint8_t* dst, const uint8_t* src, int n, int lane) {
-  const int head = min(n, static_cast<int>((4u - (reinterpret_cast<uintptr_t>(dst) & 3u)) & 3u));
+// Warp-wide copy of n bytes from shared to global memory: 16-byte aligned
+// destination vectors assembled with funnel shifts, the ragged ends byte by
+// byte.  May read up to 20 bytes past the source end.
+__device__ __forceinline__ void warp_copy_out(uint8_t* dst, const uint8_t* src, int n, int lane) {
+  const int head = min(n, static_cast<int>((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u));
   if (lane < head) dst[lane] = src[lane];
   dst += head;
   src += head;
   n -= head;
-  const int nw = n >> 2;
-  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  const int nv = n >> 4;
   const uintptr_t sa = reinterpret_cast<uintptr_t>(src);
   const uint32_t* s = reinterpret_cast<const uint32_t*>(sa & ~uintptr_t(3));
   const uint32_t sh = static_cast<uint32_t>(sa & 3u) * 8u;
-  for (int k = lane; k < nw; k += 32) d[k] = __funnelshift_r(s[k], s[k + 1], sh);
-  if (lane < (n & 3)) dst[4 * nw + lane] = src[4 * nw + lane];
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  for (int k = lane; k < nv; k += 32) {
+    const uint32_t* q = s + 4 * k;
+    const uint32_t w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3], w4 = q[4];
+    d[k] = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh), __funnelshift_r(w2, w3, sh),
+                      __funnelshift_r(w3, w4, sh));
+  }
+  if (lane < (n & 15)) dst[16 * nv + lane] = src[16 * nv + lane];
 }
 
 // String fields with more data bytes in a tile than this are copied by a
@@ -431,7 +433,6 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
   extern __shared__ __align__(128) uint8_t smem[];
   SmemHead* H = reinterpret_cast<SmemHead*>(smem);
   uint8_t* s_tile = smem + Lay::kTile;
-  uint8_t* s_stage = smem + Lay::kStage;
   uint64_t* s_dm = reinterpret_cast<uint64_t*>(smem + Lay::kDm);
   uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + Lay::kCnt);
   uint16_t* s_dex = reinterpret_cast<uint16_t*>(smem + Lay::kDex);  // data bytes before each chunk
@@ -909,18 +910,6 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       if (warp == 0) {
         const int64_t base_k = lookback_sums(J.st_bytes, t, NS, H->tile_tot, deadline, J.misc);
         if (lane < static_cast<int>(NS)) H->col_base[lane] = base_k;
-        __syncwarp();
-        if (lane == 0) {
-          // staging regions share the destination's 16-byte phase so that
-          // their aligned interiors can be bulk-stored
-          uint32_t off = 0;
-          for (uint32_t k = 0; k < NS; ++k) {
-            const uint8_t* dst = static_cast<const uint8_t*>(cols[H->str_col[k]].values) + H->col_base[k];
-            off = ((off + 15u) & ~15u) + static_cast<uint32_t>(reinterpret_cast<uintptr_t>(dst) & 15u);
-            H->stage_off[k] = off;
-            off += H->tile_tot[k];
-          }
-        }
       }
       __syncthreads();
       PP_PHASE(7);
@@ -1060,36 +1049,40 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       }
 
       PP_PHASE(11);
-      // (3) string fields into their per-column staging regions: a warp
-      // takes 32 consecutive fields at a time; each lane copies its field if
-      // short, then the warp copies the long ones together, one by one
+      // (3) string field bytes to their columns: a warp takes 32
+      // consecutive fields at a time; each lane copies its field if short,
+      // then the warp copies the long ones together, one by one.  Nothing is
+      // written past a column's capacity.
       if (NS > 0) {
         for (uint32_t base = warp * 32; base < nwin; base += NT) {
           const uint32_t g = base + lane;
-          bool is_long = false;
-          int fd = 0;
-          uint32_t nb = 0, doff = 0;
-          bool contiguous = true;
+          bool is_long = false, contiguous = true;
+          int fd = 0, e = 0;
+          uint32_t nb = 0;
+          uint8_t* gdst = nullptr;
           if (g < nwin) {
             const uint32_t fe = s_fe[g];
             const uint32_t c = (fe >> 16) & 0xFFu;
             if (c < C && TB.str_slot[c] != 0xFF && !(((fe >> 24) & 1u) && open_dead)) {
-              const int e = static_cast<int>(fe & 0x7FFFu);
+              e = static_cast<int>(fe & 0x7FFFu);
               const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & 0x7FFFu) + 1 : prev_pos + 1;
               const uint32_t da = data_before(a);
-              nb = data_before(e) - da;
+              const uint64_t off = static_cast<uint64_t>(H->col_base[TB.str_slot[c]]) +
+                                   static_cast<uint16_t>(s_fo[g] + da);
+              const uint64_t cap = cols[c].values_cap;
+              nb = off >= cap ? 0u : static_cast<uint32_t>(min(static_cast<uint64_t>(data_before(e) - da), cap - off));
               if (nb > 0) {
-                doff = H->stage_off[TB.str_slot[c]] + static_cast<uint16_t>(s_fo[g] + da);
+                gdst = static_cast<uint8_t*>(cols[c].values) + off;
                 fd = first_data(a, e);
                 contiguous = data_before(fd + static_cast<int>(nb)) == da + nb;
                 if (nb > kLongField) {
                   is_long = true;
                 } else if (contiguous) {
-                  smem_copy(s_stage + doff, s_tile + fd, static_cast<int>(nb));
+                  smem_copy(gdst, s_tile + fd, static_cast<int>(nb));
                 } else {
-                  uint8_t* dst = s_stage + doff;
-                  for (int x = fd; x < e; ++x)
-                    if ((s_dm[(x / B) * MW + ((x % B) >> 6)] >> ((x % B) & 63)) & 1ull) *dst++ = s_tile[x];
+                  uint32_t m = 0;
+                  for (int x = fd; x < e && m < nb; ++x)
+                    if ((s_dm[(x / B) * MW + ((x % B) >> 6)] >> ((x % B) & 63)) & 1ull) gdst[m++] = s_tile[x];
                 }
               }
             }
@@ -1099,19 +1092,22 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
             const int src = __ffs(static_cast<int>(longs)) - 1;
             longs &= longs - 1;
             const int lfd = __shfl_sync(0xffffffffu, fd, src);
-            const int lnb = static_cast<int>(__shfl_sync(0xffffffffu, nb, src));
-            const uint32_t ldoff = __shfl_sync(0xffffffffu, doff, src);
+            const uint32_t lnb = __shfl_sync(0xffffffffu, nb, src);
+            uint8_t* ldst = reinterpret_cast<uint8_t*>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(gdst), src));
             if (__shfl_sync(0xffffffffu, contiguous, src)) {
-              warp_smem_copy(s_stage + ldoff, s_tile + lfd, lnb, lane);
+              warp_copy_out(ldst, s_tile + lfd, static_cast<int>(lnb), lane);
             } else {  // data bytes with gaps: each lane places the bytes it holds by their rank
-              const uint32_t lfe = s_fe[base + src];
-              const int e = static_cast<int>(lfe & 0x7FFFu);
+              const int le = __shfl_sync(0xffffffffu, e, src);
               const uint32_t d0 = data_before(lfd);
-              for (int u = lfd / B; u * B < e; ++u) {
+              for (int u = lfd / B; u * B < le; ++u) {
                 for (int x = u * B + lane; x < (u + 1) * B; x += 32) {
-                  if (x < lfd || x >= e) continue;
+                  if (x < lfd || x >= le) continue;
                   const int i = x - u * B;
-                  if ((s_dm[u * MW + (i >> 6)] >> (i & 63)) & 1ull) s_stage[ldoff + (data_before(x) - d0)] = s_tile[x];
+                  if ((s_dm[u * MW + (i >> 6)] >> (i & 63)) & 1ull) {
+                    const uint32_t rank = data_before(x) - d0;
+                    if (rank < lnb) ldst[rank] = s_tile[x];
+                  }
                 }
               }
             }
@@ -1129,32 +1125,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       J.misc->done = 1u;
     }
 
-    // ------------------- write the gathered string bytes, 16 B per thread
-    if (NS > 0) {
-      PP_PHASE(8);
-      for (uint32_t k = 0; k < NS; ++k) {
-        const Col& col = cols[H->str_col[k]];
-        const uint64_t c0 = static_cast<uint64_t>(H->col_base[k]);
-        const uint64_t c1 = min(c0 + H->tile_tot[k], col.values_cap);
-        if (c1 <= c0) continue;
-        uint8_t* gbase = static_cast<uint8_t*>(col.values);
-        const uintptr_t g0 = reinterpret_cast<uintptr_t>(gbase + c0);
-        const uintptr_t g1 = reinterpret_cast<uintptr_t>(gbase + c1);
-        const uintptr_t A = (g0 + 15) & ~uintptr_t(15), Bn = g1 & ~uintptr_t(15);
-        const uint8_t* sbase = s_stage + H->stage_off[k];  // same 16-byte phase as g0
-        const int nvec = Bn > A ? static_cast<int>((Bn - A) >> 4) : 0;
-        const uint4* sv = reinterpret_cast<const uint4*>(sbase + (A - g0));
-        uint4* gv = reinterpret_cast<uint4*>(A);
-        for (int i = tid; i < nvec; i += NT) gv[i] = sv[i];
-        if (tid < 32) {
-          const uintptr_t y = tid < 16 ? g0 + tid : max(Bn, A) + (tid - 16);
-          const bool ok = tid < 16 ? (y < A && y < g1) : (y < g1);
-          if (ok) *reinterpret_cast<uint8_t*>(y) = sbase[y - g0];
-        }
-      }
-    }
-    __syncthreads();
-    PP_PHASE(9);
+    PP_PHASE(9);  // the last barrier of the round loop ends the tile
   }
 #ifdef PP_PHASE_TIMING
   if (tid == 0 && L.phase_cycles != nullptr)

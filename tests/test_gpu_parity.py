@@ -21,7 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
-CONFIGS = [1, 2, 3, 4, 5, 6, 7, 8]
+CONFIGS = list(range(1, 13))
 
 
 @pytest.fixture(scope="module")
