@@ -153,11 +153,11 @@ ShapeInfo shape_for(int cfg) {
     case 6: return shape_info_m128x6();
     case 7: return shape_info_s128();
     case 8: return shape_info_mid3();
-    case 9: return shape_info_v48();
-    case 10: return shape_info_v64();
-    case 11: return shape_info_v32();
-    case 12: return shape_info_w48();
-    default: return shape_info_mid();
+    case 9: return shape_info_y96();
+    case 10: return shape_info_z64();
+    case 11: return shape_info_w48();
+    case 12: return shape_info_big3();
+    default: return shape_info_big3();
   }
 }
 
