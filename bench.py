@@ -300,7 +300,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--partition-bytes", type=int, default=256 << 20)
+    ap.add_argument("--partition-bytes", type=int, default=512 << 20)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-inputs", type=int, default=10_000)
