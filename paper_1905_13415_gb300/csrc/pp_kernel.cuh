@@ -121,8 +121,6 @@ struct SmemLayout {
   static constexpr size_t kFo = kFe + sizeof(uint32_t) * kFcap;
   static constexpr size_t kRec = kFo + sizeof(uint16_t) * kFcap;
   static constexpr size_t kBytes = kRec + sizeof(uint16_t) * kFcap;
-  // before the field list exists, its memory holds three chunk masks
-  static_assert(kBytes - kFe >= 3 * sizeof(uint64_t) * Shape::NT * Shape::MW, "field-list memory too small");
 };
 
 // ---------------------------------------------------- look-back (1 word) ---
