@@ -112,15 +112,33 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup():
+def dist_setup(backend: str = "nccl"):
+    """One process per GPU (torchrun): each rank parses its own replica of the
+    workload; the ranks only agree on the timing."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
     return world, rank, local
+
+
+def max_over_ranks(values, world: int, device):
+    """Each timing's maximum over the ranks: the slowest replica sets the step."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def whole_job_rate(world: int, bytes_per_rank: int, step_ms: float) -> float:
+    """GB/s of all replicas together (every rank parses bytes_per_rank per step)."""
+    return world * bytes_per_rank / (step_ms * 1e-3) / 1e9
 
 
 def oracle_rate(workload_name: str, raw_sample, schema, dialect):
@@ -378,14 +396,11 @@ def main():
     clocks = sampler.stop()
     step_ms = e0.elapsed_time(e1) / args.steps
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(k_start, k_stop))
-    if world > 1:
-        t = torch.tensor([step_ms, kern_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms, kern_ms = float(t[0]), float(t[1])
+    step_ms, kern_ms = max_over_ranks([step_ms, kern_ms], world, dev)
     res = out.result()
     assert res.status == 0 and res.rows == rows
 
-    value = world * n / (step_ms * 1e-3) / 1e9
+    value = whole_job_rate(world, n, step_ms)
     peak, peak_kind = measured_peak_gbs()
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
     traffic = recorded_traffic(args.workload)
@@ -421,11 +436,8 @@ def main():
             del parts
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / ksteps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t[0])
-        e2e = {"value": round(world * n / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+        (e2e_ms,) = max_over_ranks([e2e_ms], world, dev)
+        e2e = {"value": round(whole_job_rate(world, n, e2e_ms), 3), "unit": "GB/s",
                "h2d_bytes_per_step": n, "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
                "steps": ksteps, "api": "StreamParser.parse (partitioned, overlapped, carry-over)",
                "partition_bytes": args.partition_bytes}
