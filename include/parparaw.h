@@ -172,11 +172,11 @@ typedef struct pp_parser pp_parser;
 /* Tuning options (parparaw_set_option). */
 typedef enum pp_option {
   PP_OPT_TILE_CONFIG = 1,   /* tile shape, threads x bytes per thread:
-                               0 = default (12); 1 = 32x16 (test); 2 = 64x48;
+                               0 = default (10); 1 = 32x16 (test); 2 = 64x48;
                                3 = 256x112 (2 blocks/SM); 4 = 128x208;
                                5 = 128x112; 6 = 128x112 (6 blocks/SM);
                                7 = 128x48; 8 = 256x80; 9 = 256x96;
-                               10 = 256x64; 11 = 512x48;
+                               10 = 448x64; 11 = 512x48;
                                12 = 256x112 (3 blocks/SM) */
   PP_OPT_TIMEOUT_MS = 2,    /* bound of every device-side wait (default 2000) */
   PP_OPT_GRID_LIMIT = 3,    /* 0 = one block per tile; n = at most n resident

@@ -17,7 +17,7 @@ from . import _abi
 from .parser import Batch
 
 # (config, threads x bytes per thread): the shapes worth timing for throughput
-CANDIDATES = {2: "64x48", 3: "256x112", 9: "256x96", 11: "512x48", 12: "256x112/3"}
+CANDIDATES = {2: "64x48", 9: "256x96", 10: "448x64", 11: "512x48", 12: "256x112/3"}
 
 
 def time_batch(items, reps: int = 3, warmup: int = 1, stream=None) -> float:

@@ -154,10 +154,10 @@ ShapeInfo shape_for(int cfg) {
     case 7: return shape_info_s128();
     case 8: return shape_info_mid3();
     case 9: return shape_info_y96();
-    case 10: return shape_info_z64();
+    case 10: return shape_info_t448();
     case 11: return shape_info_w48();
     case 12: return shape_info_big3();
-    default: return shape_info_big3();
+    default: return shape_info_t448();
   }
 }
 

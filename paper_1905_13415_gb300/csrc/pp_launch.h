@@ -22,7 +22,7 @@ ShapeInfo shape_info_m128x6();  // 128 threads x 112 B = 14 KiB tiles, 6 blocks 
 ShapeInfo shape_info_s128();    // 128 threads x 48 B  =  6 KiB tiles, 8 blocks / SM
 ShapeInfo shape_info_mid3();    // 256 threads x 80 B  = 20 KiB tiles, 3 blocks / SM
 ShapeInfo shape_info_y96();     // 256 threads x 96 B  = 24 KiB tiles, 3 blocks / SM
-ShapeInfo shape_info_z64();     // 256 threads x 64 B  = 16 KiB tiles, 4 blocks / SM
+ShapeInfo shape_info_t448();    // 448 threads x 64 B  = 28 KiB tiles, 2 blocks / SM
 ShapeInfo shape_info_w48();     // 512 threads x 48 B  = 24 KiB tiles, 2 blocks / SM
 ShapeInfo shape_info_big3();    // 256 threads x 112 B = 28 KiB tiles, 3 blocks / SM
 
