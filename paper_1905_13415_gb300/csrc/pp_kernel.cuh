@@ -972,14 +972,23 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       const int prev_pos = H->prev_pos;
 
       // (1) equal shares of consecutive entries: per-slot running byte
-      // positions -> s_fo (field end minus data bytes before it, mod 2^16),
-      // and records with a wrong field count (rare)
+      // positions -> s_fo (field end minus data bytes before it, mod 2^16);
+      // string field bytes to their columns (a lane copies a short field,
+      // the warp the long ones together; nothing past a column's capacity);
+      // records with a wrong field count (rare)
       {
         const uint32_t per = (nwin + NT - 1) / NT;
         const uint32_t b0 = min(tid * per, nwin), b1 = min(b0 + per, nwin);
         for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = static_cast<uint16_t>(s_cnt[k * NT + tid] + H->round_base[k]);
-        uint32_t dprev = data_before(b0 == 0 ? prev_pos + 1 : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu));
-        for (uint32_t g = b0; g < b1; ++g) {
+        int eprev = b0 == 0 ? prev_pos : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu);
+        uint32_t dprev = data_before(eprev + 1);
+        for (uint32_t i = 0; i < per; ++i) {  // the same trip count in every lane (warp-wide copies)
+          const uint32_t g = b0 + i;
+          bool is_long = false, contiguous = true;
+          int fd = 0;
+          uint32_t nb = 0;
+          uint8_t* gdst = nullptr;
+          if (g < b1) {
           const uint32_t fe = s_fe[g];
           const int e = static_cast<int>(fe & 0x7FFFu);
           const uint32_t c = (fe >> 16) & 0xFFu;
@@ -990,9 +999,29 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
               const uint16_t run = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (de - dprev));
               s_cnt[slot * NT + tid] = run;
               s_fo[g] = static_cast<uint16_t>(run - de);
+              if (de > dprev && !(((fe >> 24) & 1u) && open_dead)) {
+                const uint64_t off = static_cast<uint64_t>(H->col_base[slot]) + static_cast<uint16_t>(run - (de - dprev));
+                const uint64_t cap = cols[c].values_cap;
+                nb = off >= cap ? 0u : static_cast<uint32_t>(min(static_cast<uint64_t>(de - dprev), cap - off));
+                if (nb > 0) {
+                  gdst = static_cast<uint8_t*>(cols[c].values) + off;
+                  fd = first_data(eprev + 1, e);
+                  contiguous = data_before(fd + static_cast<int>(nb)) == dprev + nb;
+                  if (nb > kLongField) {
+                    is_long = true;
+                  } else if (contiguous) {
+                    smem_copy(gdst, s_tile + fd, static_cast<int>(nb));
+                  } else {
+                    uint32_t m = 0;
+                    for (int x = fd; x < e && m < nb; ++x)
+                      if ((s_dm[(x / B) * MW + ((x % B) >> 6)] >> ((x % B) & 63)) & 1ull) gdst[m++] = s_tile[x];
+                  }
+                }
+              }
             }
             dprev = de;
           }
+          eprev = e;
           if ((fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
             // the record ends with the wrong number of fields: reject it and
             // give the missing columns their defaults
@@ -1010,6 +1039,34 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
                   cols[c2].offsets[row + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
                 else
                   store_value(cols[c2], TB.col_type[c2], row, 0);
+              }
+            }
+          }
+          }
+          if (NS > 0) {
+            uint32_t longs = __ballot_sync(0xffffffffu, is_long);
+            while (longs) {
+              const int src = __ffs(static_cast<int>(longs)) - 1;
+              longs &= longs - 1;
+              const int lfd = __shfl_sync(0xffffffffu, fd, src);
+              const uint32_t lnb = __shfl_sync(0xffffffffu, nb, src);
+              uint8_t* ldst = reinterpret_cast<uint8_t*>(
+                  __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(gdst), src));
+              if (__shfl_sync(0xffffffffu, contiguous, src)) {
+                warp_copy_out(ldst, s_tile + lfd, static_cast<int>(lnb), lane);
+              } else {  // data bytes with gaps: each lane places the bytes it holds by their rank
+                const int le = __shfl_sync(0xffffffffu, eprev, src);  // the field's end
+                const uint32_t d0 = data_before(lfd);
+                for (int u = lfd / B; u * B < le; ++u) {
+                  for (int x = u * B + lane; x < (u + 1) * B; x += 32) {
+                    if (x < lfd || x >= le) continue;
+                    const int ix = x - u * B;
+                    if ((s_dm[u * MW + (ix >> 6)] >> (ix & 63)) & 1ull) {
+                      const uint32_t rank = data_before(x) - d0;
+                      if (rank < lnb) ldst[rank] = s_tile[x];
+                    }
+                  }
+                }
               }
             }
           }
@@ -1047,71 +1104,6 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       }
 
       PP_PHASE(11);
-      // (3) string field bytes to their columns: a warp takes 32
-      // consecutive fields at a time; each lane copies its field if short,
-      // then the warp copies the long ones together, one by one.  Nothing is
-      // written past a column's capacity.
-      if (NS > 0) {
-        for (uint32_t base = warp * 32; base < nwin; base += NT) {
-          const uint32_t g = base + lane;
-          bool is_long = false, contiguous = true;
-          int fd = 0, e = 0;
-          uint32_t nb = 0;
-          uint8_t* gdst = nullptr;
-          if (g < nwin) {
-            const uint32_t fe = s_fe[g];
-            const uint32_t c = (fe >> 16) & 0xFFu;
-            if (c < C && TB.str_slot[c] != 0xFF && !(((fe >> 24) & 1u) && open_dead)) {
-              e = static_cast<int>(fe & 0x7FFFu);
-              const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & 0x7FFFu) + 1 : prev_pos + 1;
-              const uint32_t da = data_before(a);
-              const uint64_t off = static_cast<uint64_t>(H->col_base[TB.str_slot[c]]) +
-                                   static_cast<uint16_t>(s_fo[g] + da);
-              const uint64_t cap = cols[c].values_cap;
-              nb = off >= cap ? 0u : static_cast<uint32_t>(min(static_cast<uint64_t>(data_before(e) - da), cap - off));
-              if (nb > 0) {
-                gdst = static_cast<uint8_t*>(cols[c].values) + off;
-                fd = first_data(a, e);
-                contiguous = data_before(fd + static_cast<int>(nb)) == da + nb;
-                if (nb > kLongField) {
-                  is_long = true;
-                } else if (contiguous) {
-                  smem_copy(gdst, s_tile + fd, static_cast<int>(nb));
-                } else {
-                  uint32_t m = 0;
-                  for (int x = fd; x < e && m < nb; ++x)
-                    if ((s_dm[(x / B) * MW + ((x % B) >> 6)] >> ((x % B) & 63)) & 1ull) gdst[m++] = s_tile[x];
-                }
-              }
-            }
-          }
-          uint32_t longs = __ballot_sync(0xffffffffu, is_long);
-          while (longs) {
-            const int src = __ffs(static_cast<int>(longs)) - 1;
-            longs &= longs - 1;
-            const int lfd = __shfl_sync(0xffffffffu, fd, src);
-            const uint32_t lnb = __shfl_sync(0xffffffffu, nb, src);
-            uint8_t* ldst = reinterpret_cast<uint8_t*>(
-                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(gdst), src));
-            if (__shfl_sync(0xffffffffu, contiguous, src)) {
-              warp_copy_out(ldst, s_tile + lfd, static_cast<int>(lnb), lane);
-            } else {  // data bytes with gaps: each lane places the bytes it holds by their rank
-              const int le = __shfl_sync(0xffffffffu, e, src);
-              const uint32_t d0 = data_before(lfd);
-              for (int u = lfd / B; u * B < le; ++u) {
-                for (int x = u * B + lane; x < (u + 1) * B; x += 32) {
-                  if (x < lfd || x >= le) continue;
-                  const int i = x - u * B;
-                  if ((s_dm[u * MW + (i >> 6)] >> (i & 63)) & 1ull) {
-                    const uint32_t rank = data_before(x) - d0;
-                    if (rank < lnb) ldst[rank] = s_tile[x];
-                  }
-                }
-              }
-            }
-          }
-        }
-      }
       __syncthreads();
       PP_PHASE(12);
       if (r + 1 < nrounds) next_round();
