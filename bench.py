@@ -414,7 +414,8 @@ def main():
 
         del out
         torch.cuda.empty_cache()
-        sp = StreamParser(parser, partition_bytes=args.partition_bytes, device=dev)
+        sp = StreamParser(parser, partition_bytes=args.partition_bytes, device=dev,
+                          rows_per_byte=rows / n * 1.25 + 1e-6)  # output buffers sized from the first parse
 
         def e2e_step():
             parts = sp.parse(host_in)
