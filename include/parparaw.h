@@ -181,11 +181,16 @@ typedef enum pp_option {
   PP_OPT_TIMEOUT_MS = 2,    /* bound of every device-side wait (default 2000) */
   PP_OPT_GRID_LIMIT = 3,    /* 0 = one block per tile; n = at most n resident
                                blocks looping over tiles (persistent) */
-  PP_OPT_PARTIAL_INPUT = 4  /* 1 = the input is one partition of a longer
+  PP_OPT_PARTIAL_INPUT = 4, /* 1 = the input is one partition of a longer
                                stream (Sec. 4.4): bytes after the last record
                                delimiter are an incomplete record, not emitted
                                and not an error; result.consumed reports where
                                they start.  0 (default) = the input is whole. */
+  PP_OPT_FIRST_ITEM = 5     /* testing only: the work queue starts at this tile
+                               (default 0).  The tiles before it never run, so
+                               later tiles' bounded look-back waits expire and
+                               the parse reports PP_E_TIMEOUT; the context stays
+                               usable.  Outputs of such a parse are undefined. */
 } pp_option;
 
 typedef struct pp_parser_info {

@@ -20,6 +20,7 @@ struct pp_parser {
   int tile_config = 0;
   uint64_t timeout_ns = 2000000000ull;
   int64_t grid_limit = 0;
+  uint32_t first_item = 0;
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
 };
 
@@ -60,7 +61,7 @@ __global__ void pp_init_kernel(const __grid_constant__ Launch L) {
       J.result->n_rejected = 0;
     }
   }
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *L.work_counter = 0ull;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *L.work_counter = L.first_item;
 }
 
 __device__ __forceinline__ void put_bitmap_word(uint8_t* bm, uint64_t w, uint32_t bits, uint64_t nbytes) {
@@ -475,6 +476,10 @@ extern "C" pp_status parparaw_set_option(pp_parser* P, pp_option option, int64_t
       if (value != 0 && value != 1) return PP_E_ARG;
       P->tab.partial = static_cast<uint8_t>(value);
       return PP_OK;
+    case PP_OPT_FIRST_ITEM:
+      if (value < 0 || value > 0xFFFFFFFFll) return PP_E_ARG;
+      P->first_item = static_cast<uint32_t>(value);
+      return PP_OK;
     default:
       return PP_E_ARG;
   }
@@ -544,6 +549,7 @@ extern "C" pp_status parparaw_parse(const pp_parser* P, const uint8_t* input, ui
   L.njobs = 1;
   L.total_tiles = J.ntiles;
   L.work_counter = reinterpret_cast<unsigned long long*>(scratch);
+  L.first_item = P->first_item;
   L.timeout_ns = P->timeout_ns;
   st = run_launch(L, shape, nspec_of(P->tab), P->grid_limit, P, stream, 1, J.ntiles, J.bit_words);
   cudaFreeAsync(scratch, stream);
@@ -647,6 +653,7 @@ void batch_launch_params(const BatchPlan& bp, uint8_t* dev, Launch* L) {
   L->njobs = static_cast<uint32_t>(bp.jobs.size());
   L->total_tiles = bp.total_tiles;
   L->work_counter = reinterpret_cast<unsigned long long*>(dev);
+  L->first_item = bp.first->first_item;
   L->timeout_ns = bp.first->timeout_ns;
 }
 
@@ -806,6 +813,7 @@ extern "C" pp_status parparaw_parse_noalloc(const pp_parser* P, const uint8_t* i
   L.njobs = 1;
   L.total_tiles = J.ntiles;
   L.work_counter = reinterpret_cast<unsigned long long*>(scratch);
+  L.first_item = P->first_item;
   L.timeout_ns = P->timeout_ns;
 
   // init clears everything the tile kernel needs at zero (status words,

@@ -70,7 +70,7 @@ struct Launch {
   const Col* cols;
   const Tables* tables;
   uint32_t njobs;
-  uint32_t pad;
+  uint32_t first_item;  // the work queue's first item (0; testing: later, see PP_OPT_FIRST_ITEM)
   uint64_t total_tiles;
   unsigned long long* work_counter;
   uint64_t timeout_ns;

@@ -207,3 +207,23 @@ def test_batch_mixed_formats(pp):
     for (p, data, out), ref in zip(items, refs):
         res = out.result()
         assert_same(out.to_host(res.rows), res, ref, what="batch")
+
+
+def test_expired_wait_reports_timeout_and_the_context_stays_usable(pp):
+    # Failure detection without a GPU fault: with the work queue started past
+    # tile 0 (a testing option), tile 0 never publishes, so every later tile's
+    # bounded look-back wait runs out; the parse must end with PP_E_TIMEOUT, and
+    # the next parse on the same context must be correct.
+    raw, _ = synth.records("mixed", 13, 0, 6000)
+    schema = synth.SCHEMAS["mixed"]
+    p = pp.Parser(pp.formats.rfc4180_csv(), schema, tile_config=2, timeout_ms=20)
+    data = to_dev(raw)
+    assert (len(raw) + 3071) // 3072 > 20  # many tiles wait on the missing one
+    p.set_option(pp._abi.OPT_FIRST_ITEM, 1)
+    out, res = p.parse(data, rows_cap=10000)
+    torch.cuda.synchronize()
+    assert res.status == pp._abi.E_TIMEOUT, res
+    p.set_option(pp._abi.OPT_FIRST_ITEM, 0)
+    out, res = p.parse(data)
+    torch.cuda.synchronize()
+    assert_same(out.to_host(res.rows), res, oracle_parse("csv", schema, raw), what="after a timeout")
