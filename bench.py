@@ -189,6 +189,46 @@ def run_reference(args):
     return 0
 
 
+def run_other_configs(args, dev, log):
+    """The two other plain-parse configurations: the 1 MB mixed CSV (latency of
+    one parse: median of many, inputs resident) and the 1e9-byte trip-record
+    CSV (GB/s, timed like the main workload)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1905_13415_gb300 import Parser, formats
+
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, size, reps in (("mixed", 1_000_000, 200), ("trip", 1_000_000_000, 10)):
+        wl, seed_off, _, desc = WORKLOADS[name]
+        host = torch.empty(size, dtype=torch.uint8, pin_memory=True)
+        n, rows = synth.generate_into(wl, synth.BASE_SEED + seed_off, size, host.data_ptr(), size)
+        data = host[:n].to(dev)
+        p = Parser(formats.by_name(synth.DIALECT[wl]), synth.SCHEMAS[wl], tile_config=args.tile_config)
+        o, res = p.parse(data, rows_cap=rows + 16)
+        assert res.status == 0 and res.rows == rows, (name, res)
+        for _ in range(3):
+            p.parse_into(data, o, stream=stream)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.parse_into(data, o, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        med = float(np.median(ms))
+        out[name] = {"workload": desc, "input_bytes": n, "rows": rows, "ms_median": round(med, 4),
+                     "GB/s": round(n / (med * 1e-3) / 1e9, 3), "runs": reps,
+                     "note": "one parse (init, tile, finalize kernels) per run, input resident"}
+        log(f"{name}: {n} B in {med:.3f} ms (median of {reps})")
+        del o, data, host
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_batched(args, dev, log):
     """Config 4: 10,000 inputs (log-normal sizes 1 KB..64 MB, ~6e9 B, half CSV,
     half web logs) in one persistent launch per step, tile shape autotuned."""
@@ -320,6 +360,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--partition-bytes", type=int, default=512 << 20)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-others", action="store_true", help="skip the 1 MB and 1 GB plain-parse lines")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-inputs", type=int, default=10_000)
     ap.add_argument("--batch-bytes", type=int, default=6_000_000_000)
@@ -458,7 +499,9 @@ def main():
     def log(msg):
         print(msg, file=sys.stderr, flush=True)
 
-    batched = served = None
+    batched = served = others = None
+    if rank == 0 and world == 1 and not args.no_others:
+        others = run_other_configs(args, dev, log)
     if rank == 0 and world == 1 and not args.no_batch:
         batched = run_batched(args, dev, log)
     if rank == 0 and world == 1 and not args.no_serve:
@@ -483,6 +526,7 @@ def main():
             "gpu_launches": 3 * args.steps,
             "batched": batched,
             "served": served,
+            "other_configs": others,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

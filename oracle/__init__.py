@@ -61,6 +61,20 @@ class _Result(ctypes.Structure):
     ]
 
 
+class _Inference(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("min_fields", ctypes.c_uint32),
+        ("max_fields", ctypes.c_uint32),
+        ("records", ctypes.c_int64),
+        ("first_invalid_offset", ctypes.c_int64),
+        ("type", ctypes.c_uint8 * MAX_COLUMNS),
+    ]
+
+
+NO_TYPE = 0xFF
+INFER_MAX_FIELDS = 256
+
 _lib = None
 
 
@@ -87,6 +101,9 @@ def lib():
         L.ppo_free.argtypes = [ctypes.POINTER(_Result)]
         L.ppo_convert.argtypes = [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
         L.ppo_convert.restype = ctypes.c_int
+        L.ppo_infer.argtypes = [ctypes.POINTER(_Format), ctypes.c_void_p, ctypes.c_size_t,
+                                ctypes.POINTER(_Inference)]
+        L.ppo_infer.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -305,3 +322,21 @@ def parse(fmt: Format, types, data) -> ParseResult:
                            res.first_invalid_offset, cols, row_valid)
     finally:
         lib().ppo_free(ctypes.byref(res))
+
+
+@dataclass
+class Inference:
+    status: int
+    min_fields: int
+    max_fields: int
+    records: int
+    first_invalid_offset: int
+    types: list  # per field position: INT32 / INT64 / FLOAT64 / STRING, or NO_TYPE
+
+
+def infer(fmt: Format, data) -> Inference:
+    """Sec. 4.3: column-count and numeric type inference (see ppo_infer)."""
+    buf = np.frombuffer(data, dtype=np.uint8) if not isinstance(data, np.ndarray) else data
+    r = _Inference()
+    lib().ppo_infer(ctypes.byref(fmt._c), buf.ctypes.data, len(buf), ctypes.byref(r))
+    return Inference(r.status, r.min_fields, r.max_fields, r.records, r.first_invalid_offset, list(r.type))

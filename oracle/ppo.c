@@ -443,3 +443,82 @@ void ppo_free(ppo_result* r) {
   free(r->row_valid);
   memset(r, 0, sizeof(*r));
 }
+
+/* ------------------------------------------- Sec. 4.3: type inference */
+
+/* rank in the chain int32 < int64 < float64 < string of a field's narrowest type */
+static int infer_rank(const uint8_t* text, size_t len) {
+  uint8_t v[8];
+  if (len <= PPO_NUMERIC_MAX_LEN) {
+    if (ppo_convert(PPO_INT32, text, len, v) == PPO_CONV_OK) return 1;
+    if (ppo_convert(PPO_INT64, text, len, v) == PPO_CONV_OK) return 2;
+    if (ppo_convert(PPO_FLOAT64, text, len, v) == PPO_CONV_OK) return 3;
+  }
+  return 4;
+}
+
+int ppo_infer(const ppo_format* f, const uint8_t* in, size_t len, ppo_inference* out) {
+  static const uint8_t type_of_rank[5] = {PPO_NO_TYPE, PPO_INT32, PPO_INT64, PPO_FLOAT64, PPO_STRING};
+  int rank[PPO_MAX_COLUMNS] = {0};
+  uint8_t text[PPO_NUMERIC_MAX_LEN + 1];
+  size_t tlen = 0;       /* data bytes of the current field (only the first ones are kept) */
+  uint32_t field = 0;    /* position of the current field in its record */
+  memset(out, 0, sizeof(*out));
+  out->min_fields = 0xFFFFFFFFu;
+  int64_t first_invalid = -1;
+  size_t since_record = 0;
+  uint8_t s = f->start_state;
+  /* a field ends: its narrowest type widens its position's type */
+  #define END_FIELD()                                                   \
+    do {                                                                \
+      if (field < PPO_MAX_COLUMNS && tlen > 0) {                        \
+        const int r = infer_rank(text, tlen);                           \
+        if (r > rank[field]) rank[field] = r;                           \
+      }                                                                 \
+      tlen = 0;                                                         \
+    } while (0)
+  /* a record ends with field + 1 fields */
+  #define END_RECORD()                                                  \
+    do {                                                                \
+      uint32_t n = field + 1 < PPO_INFER_MAX_FIELDS ? field + 1 : PPO_INFER_MAX_FIELDS; \
+      if (n < out->min_fields) out->min_fields = n;                     \
+      if (n > out->max_fields) out->max_fields = n;                     \
+      out->records++;                                                   \
+      field = 0;                                                        \
+    } while (0)
+  for (size_t i = 0; i < len; ++i) {
+    const uint8_t g = f->group_of[in[i]];
+    const uint8_t tag = f->emit[g][s];
+    const uint8_t nxt = f->next[g][s];
+    if (f->invalid_state != PPO_NO_STATE && nxt == f->invalid_state && s != f->invalid_state &&
+        first_invalid < 0)
+      first_invalid = (int64_t)i;
+    switch (tag) {
+      case PPO_DATA:
+        if (tlen <= PPO_NUMERIC_MAX_LEN) text[tlen] = in[i];
+        tlen++;
+        break;
+      case PPO_FIELD: END_FIELD(); field++; break;
+      case PPO_RECORD: END_FIELD(); END_RECORD(); break;
+      default: break;
+    }
+    since_record = (tag == PPO_RECORD) ? 0 : since_record + 1;
+    s = nxt;
+  }
+  const int accepting = (f->accept_mask >> s) & 1u;
+  if (since_record > 0 && accepting) {
+    END_FIELD();
+    END_RECORD();
+  }
+  #undef END_FIELD
+  #undef END_RECORD
+  if (out->records == 0) out->min_fields = 0;
+  for (int c = 0; c < PPO_MAX_COLUMNS; ++c) out->type[c] = type_of_rank[rank[c]];
+  out->status = PPO_OK;
+  if (first_invalid >= 0)
+    out->status = PPO_E_INVALID_INPUT;
+  else if (!accepting)
+    out->status = PPO_E_UNTERMINATED;
+  out->first_invalid_offset = first_invalid;
+  return 0;
+}

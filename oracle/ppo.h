@@ -114,6 +114,25 @@ void ppo_free(ppo_result* r);
  * int32/int64/double bit pattern in its low bytes. Returns PPO_CONV_*. */
 int ppo_convert(uint32_t type, const uint8_t* text, size_t len, void* out);
 
+/* Sec. 4.3 (capabilities): column-count and numeric type inference.  The
+ * records are those ppo_parse finds (same tags, same trailing-record rule).
+ * min/max_fields: the fewest and the most fields of a record (a count
+ * saturates at PPO_INFER_MAX_FIELDS; both 0 without records).  type[c]: the
+ * widest, in the chain int32 < int64 < float64 < string, of the narrowest
+ * types of the non-empty fields at position c (each field's narrowest type is
+ * the first of int32, int64, float64 whose conversion accepts its text, else
+ * string); PPO_NO_TYPE when position c holds no non-empty field. */
+#define PPO_INFER_MAX_FIELDS 256
+#define PPO_NO_TYPE 0xFF
+typedef struct ppo_inference {
+  int32_t status;
+  uint32_t min_fields, max_fields;
+  int64_t records;
+  int64_t first_invalid_offset;
+  uint8_t type[PPO_MAX_COLUMNS];
+} ppo_inference;
+int ppo_infer(const ppo_format* f, const uint8_t* in, size_t len, ppo_inference* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -301,3 +301,43 @@ def test_bytes_total_counts_dropped_partial_record():
     r = O.parse(O.csv6(), [O.STRING, O.STRING], b'ab,c\nde,"f')
     assert r.status == O.E_UNTERMINATED and r.rows == 1
     assert r.columns[0].bytes_total == 4 and r.columns[1].bytes_total == 2
+
+
+# ---------------------------------------------- Sec. 4.3: type inference
+
+@pytest.mark.parametrize("raw,records,mn,mx,types", [
+    (b"1,2.5,x\n3,4,y\n", 2, 3, 3, [O.INT32, O.FLOAT64, O.STRING]),    # widest of each position
+    (b"1\n2,3\n", 2, 1, 2, [O.INT32, O.INT32]),                         # ragged records
+    (b"2147483648,1\n", 1, 2, 2, [O.INT64, O.INT32]),                   # 2^31 needs int64
+    (b"-5,,abc\n", 1, 3, 3, [O.INT32, O.NO_TYPE, O.STRING]),            # empty: no type
+    (b"1.5e3,007\n", 1, 2, 2, [O.STRING, O.INT32]),                     # no exponent syntax
+    (b"99999999999999999999,1\n", 1, 2, 2, [O.STRING, O.INT32]),        # beyond int64 and 2^53
+    (b'"12",""\n', 1, 2, 2, [O.INT32, O.NO_TYPE]),                      # quotes are not data
+    (b"a,b", 1, 2, 2, [O.STRING, O.STRING]),                            # trailing record
+    (b"", 0, 0, 0, []),
+])
+def test_inference_worked_examples(raw, records, mn, mx, types):
+    r = O.infer(O.csv6(), raw)
+    assert (r.status, r.records, r.min_fields, r.max_fields) == (O.OK, records, mn, mx)
+    assert r.types[: len(types)] == types and all(t == O.NO_TYPE for t in r.types[len(types):])
+
+
+def test_inference_saturates_the_field_count():
+    r = O.infer(O.csv6(), b",".join(b"%d" % i for i in range(300)) + b"\n1\n")
+    assert (r.min_fields, r.max_fields) == (1, O.INFER_MAX_FIELDS)
+    assert r.types[:64] == [O.INT32] * 64  # only the first 64 positions are typed
+
+
+@pytest.mark.parametrize("workload", ["mixed", "trip", "review", "log"])
+def test_inference_agrees_with_the_schema_and_the_parse(workload):
+    # the generator writes every record with the schema's field count, and a
+    # parse with the inferred types (no type -> string) rejects nothing
+    raw, _ = synth.records(workload, 41, 0, 400)
+    fmt = O.csv6() if synth.DIALECT[workload] == "csv" else O.log8()
+    r = O.infer(fmt, raw)
+    C = len(synth.SCHEMAS[workload])
+    assert r.status == O.OK and r.records == 400 and r.min_fields == r.max_fields == C
+    types = [O.STRING if t == O.NO_TYPE else t for t in r.types[:C]]
+    assert O.parse(fmt, types, raw).n_rejected == 0
+    if workload == "trip":  # columns the generator writes as small integers and 2-decimal floats
+        assert types[0] == O.INT32 and types[4] == O.FLOAT64 and types[1] == O.STRING
