@@ -224,6 +224,21 @@ def run_other_configs(args, dev, log):
                      "GB/s": round(n / (med * 1e-3) / 1e9, 3), "runs": reps,
                      "note": "one parse (init, tile, finalize kernels) per run, input resident"}
         log(f"{name}: {n} B in {med:.3f} ms (median of {reps})")
+        if name == "trip":  # column-count and type inference over the same input (Sec. 4.3)
+            inf = p.infer(data)
+            assert inf.status == 0 and inf.records == rows
+            t = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                p.infer(data, stream=stream)  # includes reading the 96-byte result back
+                e1.record(stream)
+                e1.synchronize()
+                t.append(e0.elapsed_time(e1))
+            imed = float(np.median(t))
+            out["trip_infer"] = {"input_bytes": n, "ms_median": round(imed, 4),
+                                 "GB/s": round(n / (imed * 1e-3) / 1e9, 3), "runs": reps,
+                                 "min_fields": inf.min_fields, "max_fields": inf.max_fields}
         del o, data, host
         torch.cuda.empty_cache()
     return out

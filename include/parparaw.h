@@ -293,6 +293,36 @@ void parparaw_batch_destroy(pp_batch* batch);
 pp_status parparaw_parse_noalloc(const pp_parser* parser, const uint8_t* input, uint64_t len,
                                  const pp_columns* out, void* stream);
 
+/* Column-count and numeric type inference (Sec. 4.3, "Capabilities"): parses
+ * the input with the parser's DFA and symbol groups (its schema is ignored)
+ * and reports the fewest and the most fields of a record, and for every field
+ * position c < PP_MAX_COLUMNS the type that holds each of its non-empty
+ * fields: the widest, in the chain PP_INT32 < PP_INT64 < PP_FLOAT64 <
+ * PP_STRING, of the fields' narrowest types (a field's narrowest type is the
+ * first of int32, int64, float64 whose conversion accepts its text, else
+ * string).  Records are found exactly as by parparaw_parse.
+ *   - result: device memory, written on the stream.  status as in
+ *     pp_parse_result (never PP_E_CAPACITY); records = records found;
+ *     min/max_fields saturate at PP_INFER_MAX_FIELDS and are 0 without
+ *     records; type[c] = PP_TYPE_NONE where position c holds no non-empty
+ *     field.
+ *   - Runs the default tile shape whatever PP_OPT_TILE_CONFIG says.
+ *   - Returns PP_E_ARG for NULL arguments, PP_E_NOMEM / PP_E_CUDA on
+ *     allocation or launch failure. */
+#define PP_INFER_MAX_FIELDS 256
+#define PP_TYPE_NONE 0xFF
+typedef struct pp_inference {
+  int32_t status;
+  uint32_t min_fields, max_fields;
+  uint32_t pad;
+  int64_t records;
+  int64_t first_invalid_offset;
+  uint8_t type[PP_MAX_COLUMNS];
+} pp_inference;
+
+pp_status parparaw_infer(const pp_parser* parser, const uint8_t* input, uint64_t len,
+                         pp_inference* result, void* stream);
+
 /* Records the two CUDA events (cudaEvent_t passed as void*) on the stream
  * immediately before and after the main parse kernel of every later parse or
  * batch made with this parser, so that a caller can time that kernel alone.

@@ -23,7 +23,7 @@ OPT_TILE_CONFIG, OPT_TIMEOUT_MS, OPT_GRID_LIMIT, OPT_PARTIAL_INPUT, OPT_FIRST_IT
 EXPORTED = ["parparaw_create", "parparaw_destroy", "parparaw_set_option", "parparaw_get_info",
             "parparaw_parse", "parparaw_parse_batch", "parparaw_set_kernel_events",
             "parparaw_status_string", "parparaw_parse_noalloc", "parparaw_batch_create",
-            "parparaw_batch_launch", "parparaw_batch_destroy"]
+            "parparaw_batch_launch", "parparaw_batch_destroy", "parparaw_infer"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -75,6 +75,18 @@ class pp_parser_info(ctypes.Structure):
 
 RESULT_BYTES = ctypes.sizeof(pp_parse_result)
 
+INFER_MAX_FIELDS = 256
+TYPE_NONE = 0xFF
+
+
+class pp_inference(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("min_fields", ctypes.c_uint32), ("max_fields", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("records", ctypes.c_int64), ("first_invalid_offset", ctypes.c_int64),
+                ("type", ctypes.c_uint8 * 64)]
+
+
+INFERENCE_BYTES = ctypes.sizeof(pp_inference)
+
 _lib = None
 
 
@@ -117,6 +129,8 @@ def load():
     L.parparaw_parse_batch.restype = ctypes.c_int
     L.parparaw_set_kernel_events.argtypes = [vp, vp, vp]
     L.parparaw_set_kernel_events.restype = ctypes.c_int
+    L.parparaw_infer.argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
+    L.parparaw_infer.restype = ctypes.c_int
     L.parparaw_status_string.argtypes = [ctypes.c_int]
     L.parparaw_status_string.restype = ctypes.c_char_p
     _lib = L

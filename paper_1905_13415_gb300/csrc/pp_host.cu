@@ -58,7 +58,10 @@ __global__ void pp_init_kernel(const __grid_constant__ Launch L) {
       M->final_state = TB.start_state;
       M->last_record_end = 0;
       for (int k = 0; k < PP_MAX_STRING_COLUMNS; ++k) M->bytes_total[k] = 0;
-      J.result->n_rejected = 0;
+      for (int k = 0; k < PP_MAX_COLUMNS; ++k) M->inf_rank[k] = 0;
+      M->inf_min_fields = 0xFFFFFFFFu;
+      M->inf_max_fields = 0;
+      if (J.result != nullptr) J.result->n_rejected = 0;
     }
   }
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *L.work_counter = L.first_item;
@@ -131,6 +134,31 @@ __global__ void pp_finalize_kernel(const __grid_constant__ Launch L) {
       res->consumed = TB.partial ? static_cast<int64_t>(M.last_record_end) : static_cast<int64_t>(J.len);
     }
     __syncthreads();
+  }
+}
+
+// The inference result of the single job of an inference launch.
+__global__ void pp_infer_finalize_kernel(const __grid_constant__ Launch L, pp_inference* out) {
+  const Job& J = L.job0;
+  const Tables& TB = L.tables0;
+  const Misc& M = *J.misc;
+  const int c = threadIdx.x;
+  if (c < PP_MAX_COLUMNS) {
+    const uint8_t of_rank[5] = {PP_TYPE_NONE, PP_INT32, PP_INT64, PP_FLOAT64, PP_STRING};
+    out->type[c] = of_rank[min(M.inf_rank[c], 4u)];
+  }
+  if (c == 0) {
+    const bool ok_run = (J.ntiles == 0) || M.done;
+    int32_t status = PP_OK;
+    if (M.timeout || !ok_run) status = PP_E_TIMEOUT;
+    else if (M.first_invalid != ~0ull) status = PP_E_INVALID_INPUT;
+    else if (!((TB.accept_mask >> M.final_state) & 1u)) status = PP_E_UNTERMINATED;
+    out->status = status;
+    out->records = ok_run ? M.rows : 0;
+    out->min_fields = out->records > 0 && M.inf_min_fields != 0xFFFFFFFFu ? M.inf_min_fields : 0u;
+    out->max_fields = out->records > 0 ? M.inf_max_fields : 0u;
+    out->pad = 0;
+    out->first_invalid_offset = M.first_invalid == ~0ull ? -1 : static_cast<int64_t>(M.first_invalid);
   }
 }
 
@@ -504,6 +532,81 @@ extern "C" pp_status parparaw_set_kernel_events(pp_parser* P, void* start_event,
   P->ev_start = static_cast<cudaEvent_t>(start_event);
   P->ev_stop = static_cast<cudaEvent_t>(stop_event);
   return PP_OK;
+}
+
+extern "C" pp_status parparaw_infer(const pp_parser* P, const uint8_t* input, uint64_t len,
+                                    pp_inference* result, void* stream_) {
+  if (P == nullptr || result == nullptr || (input == nullptr && len > 0)) return PP_E_ARG;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const ShapeInfo shape = shape_for(0);
+  if (shape.infer_kernel == nullptr) return PP_E_UNSUPPORTED;
+  Launch* Lp = new (std::nothrow) Launch();
+  if (Lp == nullptr) return PP_E_NOMEM;
+  Launch& L = *Lp;
+  std::memset(&L, 0, sizeof(L));
+  // the parser's DFA; PP_MAX_COLUMNS field positions, none of them stored
+  L.tables0 = P->tab;
+  L.tables0.num_columns = PP_MAX_COLUMNS;
+  L.tables0.num_str = 0;
+  L.tables0.num_num = 0;
+  L.tables0.partial = 0;
+  for (int c = 0; c < PP_MAX_COLUMNS; ++c) {
+    L.tables0.col_type[c] = PP_STRING;
+    L.tables0.str_slot[c] = 0xFF;
+    L.tables0.num_slot[c] = 0xFF;
+  }
+  Job& J = L.job0;
+  J.input = input;
+  J.len = len;
+  J.head = len > 0 ? (reinterpret_cast<uintptr_t>(input) & 15u) : 0;
+  J.ntiles = len > 0 ? (J.head + len + shape.tile_bytes - 1) / shape.tile_bytes : 0;
+  J.tile_base = 0;
+  J.rows_cap = ~0ull;  // no row is stored
+  J.bit_words = 0;
+  J.row_valid = nullptr;
+  J.result = nullptr;
+  const ScratchPlan plan = plan_scratch(64, J.ntiles, 0, 0, 0);
+  uint8_t* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), plan.total, stream);
+  if (e != cudaSuccess) {
+    delete Lp;
+    return map_err(e);
+  }
+  fill_job(J, plan, scratch);
+  L.njobs = 1;
+  L.total_tiles = J.ntiles;
+  L.work_counter = reinterpret_cast<unsigned long long*>(scratch);
+  L.first_item = 0;
+  L.timeout_ns = P->timeout_ns;
+  pp_status st = PP_OK;
+  int dev = 0;
+  DeviceProps props;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess || (e = device_props(dev, &props)) != cudaSuccess) {
+    st = map_err(e);
+  } else {
+    const uint32_t gx_init = static_cast<uint32_t>(
+        std::max<uint64_t>(1, std::min<uint64_t>((J.ntiles + kBlockInit - 1) / kBlockInit, 1024)));
+    pp_init_kernel<<<gx_init, kBlockInit, 0, stream>>>(L);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && L.total_tiles > 0) {
+      const void* kern = shape.infer_kernel(nspec_of(P->tab));
+      int per_sm = 0;
+      if ((e = kernel_occupancy(kern, shape.threads, shape.smem_bytes, dev, &per_sm)) == cudaSuccess) {
+        const uint64_t grid = std::min<uint64_t>(L.total_tiles, static_cast<uint64_t>(per_sm) * props.sms);
+        void* args[] = {&L};
+        e = cudaLaunchKernel(kern, dim3(static_cast<uint32_t>(grid)), dim3(shape.threads), args,
+                             shape.smem_bytes, stream);
+      }
+    }
+    if (e == cudaSuccess) {
+      pp_infer_finalize_kernel<<<1, PP_MAX_COLUMNS, 0, stream>>>(L, result);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = map_err(e);
+  }
+  cudaFreeAsync(scratch, stream);
+  delete Lp;
+  return st;
 }
 
 extern "C" pp_status parparaw_parse(const pp_parser* P, const uint8_t* input, uint64_t len,

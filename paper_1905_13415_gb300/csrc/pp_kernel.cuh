@@ -424,7 +424,11 @@ __device__ __forceinline__ void store_value(const Col& col, uint32_t type, uint6
 
 // ------------------------------------------------------------- kernel ---
 
-template <class Shape, int NSPEC>
+// INFER: the inference form (parparaw_infer): the same pipeline, but each
+// record's field count and each field's narrowest numeric type are reduced
+// per tile in shared memory (the per-column sums, unused then) and folded into
+// the job's Misc; nothing is written to the columns.
+template <class Shape, int NSPEC, bool INFER = false>
 __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const __grid_constant__ Launch L) {
   constexpr int NT = Shape::NT, VPT = Shape::VPT, B = Shape::B, T = Shape::T, MW = Shape::MW;
   using Lay = SmemLayout<Shape>;
@@ -475,6 +479,10 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     __syncthreads();
     const unsigned long long item = H->item;
     if (item >= L.total_tiles) break;
+    uint32_t* s_inf = reinterpret_cast<uint32_t*>(s_cnt);  // INFER: ranks [0, 64), min / max fields
+    if constexpr (INFER) {
+      if (tid < PP_MAX_COLUMNS + 2) s_inf[tid] = tid == PP_MAX_COLUMNS ? 0xFFFFFFFFu : 0u;
+    }
     if (H->job_loaded != static_cast<int32_t>(H->job)) {
       const Job& src = L.jobs ? L.jobs[H->job] : L.job0;
       const Col* csrc = L.jobs ? (L.cols + src.col0) : L.cols0;
@@ -1022,7 +1030,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
             dprev = de;
           }
           eprev = e;
-          if ((fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
+          if (!INFER && (fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
             // the record ends with the wrong number of fields: reject it and
             // give the missing columns their defaults
             uint32_t klo = 0, khi = nrec_win - 1;
@@ -1080,6 +1088,72 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       // at least as many as threads: lanes of a warp then take consecutive
       // records column by column)
       const uint32_t G = max(1u, min(C, static_cast<uint32_t>(NT) / nrec_win));
+      if constexpr (INFER) {
+        // (2') inference: the fields of each record that ends here, and the
+        // narrowest type of every non-empty field that starts here
+        for (uint32_t j = tid; j < nrec_win * G; j += NT) {
+          const uint32_t k = j / G, sub = j - k * G;
+          const uint32_t gb = s_rec[k], ge = k + 1 < nrec_win ? s_rec[k + 1] : nwin;
+          if (sub == 0 && ge > gb) {
+            const uint32_t fl = s_fe[ge - 1];
+            if ((fl & 0x8000u) && !(((fl >> 24) & 1u) && open_dead)) {
+              const uint32_t n = min(((fl >> 16) & 0xFFu) + 1u, static_cast<uint32_t>(PP_INFER_MAX_FIELDS));
+              atomicMin(&s_inf[PP_MAX_COLUMNS], n);
+              atomicMax(&s_inf[PP_MAX_COLUMNS + 1], n);
+            }
+          }
+          for (uint32_t g = gb + sub; g < ge; g += G) {
+            const uint32_t fe = s_fe[g];
+            const uint32_t c = (fe >> 16) & 0xFFu;
+            const bool open = (fe >> 24) & 1u;
+            if (c >= PP_MAX_COLUMNS || (open && open_dead)) break;
+            if (!(f0 + g > 0 || t == 0)) continue;  // started in an earlier tile, typed there
+            const int e = static_cast<int>(fe & 0x7FFFu);
+            const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & 0x7FFFu) + 1 : (f0 == 0 ? P0 : prev_pos + 1);
+            const bool ended = !open || last_tile;
+            // the field's data bytes (as in convert_field), then the first
+            // type of int32, int64, float64 that takes them, else string
+            const int n_in = static_cast<int>(data_before(e) - data_before(a));
+            uint8_t buf[kNumericMaxLen + 1];
+            const uint8_t* txt = buf;
+            int m = 0;
+            if (ended && n_in == e - a) {
+              txt = s_tile + a;
+              m = n_in;
+            } else {
+              for (int y = a; y < e && m <= kNumericMaxLen; ++y) {
+                const int u = y / B, i = y - u * B;
+                if ((s_dm[u * MW + (i >> 6)] >> (i & 63)) & 1ull) buf[m++] = s_tile[y];
+              }
+              if (!ended && m <= kNumericMaxLen) {
+                uint32_t s = tile_send;
+                for (uint64_t gg = v1; gg < VL; ++gg) {
+                  const uint8_t b = vbase[gg];
+                  const uint32_t grp = TB.group_of[b];
+                  const uint32_t tag = (TB.emit[grp] >> (2 * s)) & 3u;
+                  s = vget(TB.trans[grp], s);
+                  if (tag == PP_TAG_DATA) {
+                    buf[m++] = b;
+                    if (m > kNumericMaxLen) break;
+                  } else if (tag != PP_TAG_CONTROL) {
+                    break;
+                  }
+                  if (s == TB.invalid_state) break;
+                }
+              }
+            }
+            if (m == 0) continue;  // empty: no type
+            uint32_t rank = 4;
+            uint64_t v;
+            if (m <= kNumericMaxLen) {
+              if (convert_value(PP_INT32, txt, m, &v) == kConvOk) rank = 1;
+              else if (convert_value(PP_INT64, txt, m, &v) == kConvOk) rank = 2;
+              else if (convert_value(PP_FLOAT64, txt, m, &v) == kConvOk) rank = 3;
+            }
+            atomicMax(&s_inf[c], rank);
+          }
+        }
+      } else
       for (uint32_t j = tid; j < nrec_win * G; j += NT) {
         const uint32_t k = j / G, sub = j - k * G;
         const uint64_t row = tile_row0 + rr0 + k;
@@ -1107,6 +1181,11 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       __syncthreads();
       PP_PHASE(12);
       if (r + 1 < nrounds) next_round();
+    }
+    if constexpr (INFER) {  // after the round loop's last barrier
+      if (tid < PP_MAX_COLUMNS && s_inf[tid]) atomicMax(&J.misc->inf_rank[tid], s_inf[tid]);
+      if (tid == PP_MAX_COLUMNS && s_inf[tid] != 0xFFFFFFFFu) atomicMin(&J.misc->inf_min_fields, s_inf[tid]);
+      if (tid == PP_MAX_COLUMNS + 1 && s_inf[tid]) atomicMax(&J.misc->inf_max_fields, s_inf[tid]);
     }
     if (last_tile && tid == 0) {
       J.misc->rows = static_cast<int64_t>(tile_row0 + rec_tile + (trailing ? 1u : 0u));  // read by the finalize kernel only

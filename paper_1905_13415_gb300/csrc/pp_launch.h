@@ -10,6 +10,7 @@ struct ShapeInfo {
   int tile_bytes = 0;
   size_t smem_bytes = 0;
   const void* (*kernel)(int nspec) = nullptr;  // pp_tile_kernel<Shape, NSPEC>
+  const void* (*infer_kernel)(int nspec) = nullptr;  // its inference form (default shape only)
 };
 
 // tile configurations selectable with PP_OPT_TILE_CONFIG

@@ -39,6 +39,10 @@ struct Misc {
   uint32_t pad;
   unsigned long long last_record_end;  // partial inputs: atomicMax of (last RD + 1)
   int64_t bytes_total[PP_MAX_STRING_COLUMNS];
+  // inference (parparaw_infer): per field position the widest rank of the
+  // chain int32 (1) < int64 (2) < float64 (3) < string (4); fields per record
+  uint32_t inf_rank[PP_MAX_COLUMNS];
+  uint32_t inf_min_fields, inf_max_fields;
 };
 
 // One input of a launch.

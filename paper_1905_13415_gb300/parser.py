@@ -51,6 +51,17 @@ class Result:
         return self.status == _abi.OK
 
 
+@dataclass
+class Inference:
+    """Column-count and numeric type inference of one input (Sec. 4.3)."""
+    status: int
+    records: int
+    min_fields: int
+    max_fields: int
+    first_invalid_offset: int
+    types: list  # per field position: a pp_type code, or TYPE_NONE (no non-empty field)
+
+
 class Output:
     """Caller-owned device buffers for one parse (Arrow-like columns)."""
 
@@ -204,6 +215,17 @@ class Parser:
                                       _stream(stream))
         if rc != _abi.OK:
             raise ParparawError(rc, "parparaw_parse")
+
+    def infer(self, data: torch.Tensor, stream=None) -> Inference:
+        """Fields per record and the narrowest type of each field position
+        (parparaw_infer; this parser's schema is ignored).  Synchronises."""
+        buf = torch.zeros(_abi.INFERENCE_BYTES, dtype=torch.uint8, device=data.device)
+        st = self._lib.parparaw_infer(self.handle, _ptr(data) if data.numel() else None, data.numel(), _ptr(buf),
+                                      _stream(stream))
+        if st != _abi.OK:
+            raise ParparawError(st, "parparaw_infer")
+        r = _abi.pp_inference.from_buffer_copy(buf.cpu().numpy().tobytes())
+        return Inference(r.status, r.records, r.min_fields, r.max_fields, r.first_invalid_offset, list(r.type))
 
     def parse(self, data: torch.Tensor, rows_cap: int | None = None, stream=None) -> tuple[Output, Result]:
         """Parses with outputs sized from the input; retries once with the
