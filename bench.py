@@ -480,7 +480,7 @@ def main():
         for _ in range(max(1, min(args.warmup, 2))):
             got_rows, parts = e2e_step()
         assert got_rows == rows, (got_rows, rows)
-        d2h = sum(sum(v.numel() * v.element_size() for v in col.values()) + x.row_valid.numel()
+        d2h = sum(sum(v.numel() * v.element_size() for v in col.values() if v is not None) + x.row_valid.numel()
                   for x in parts for col in x.columns)
         del parts
         if world > 1:

@@ -72,7 +72,11 @@ typedef enum pp_tag {
  *                    seconds since 1970-01-01 UTC (proleptic Gregorian)
  *   PP_DATE_D        YYYY-MM-DD -> int32 days since 1970-01-01
  *   PP_TIMESTAMP_CLF dd/Mon/yyyy:hh:mm:ss +hhmm (Common Log Format) -> int64
- *                    seconds, UTC */
+ *                    seconds, UTC
+ *   PP_SKIP          a column that is not selected (Sec. 4.3, selecting
+ *                    columns): its fields count towards the record's fields
+ *                    but are neither converted nor stored; its pp_column needs
+ *                    no buffers (values, offsets and validity may be NULL) */
 typedef enum pp_type {
   PP_STRING = 0,
   PP_INT32 = 1,
@@ -80,7 +84,8 @@ typedef enum pp_type {
   PP_FLOAT64 = 3,
   PP_TIMESTAMP_S = 4,
   PP_DATE_D = 5,
-  PP_TIMESTAMP_CLF = 6
+  PP_TIMESTAMP_CLF = 6,
+  PP_SKIP = 7
 } pp_type;
 
 /* DFA of the format (Sec. 3.1; Sec. 4.5, Table 1: one row of transitions per

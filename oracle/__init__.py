@@ -26,7 +26,7 @@ MAX_COLUMNS = 64
 NO_STATE = 0xFF
 
 DATA, FIELD, RECORD, CONTROL = 0, 1, 2, 3
-STRING, INT32, INT64, FLOAT64, TIMESTAMP_S, DATE_D, TIMESTAMP_CLF = range(7)
+STRING, INT32, INT64, FLOAT64, TIMESTAMP_S, DATE_D, TIMESTAMP_CLF, SKIP = range(8)
 OK, E_INVALID_INPUT, E_UNTERMINATED = 0, -4, -5
 CONV_OK, CONV_EMPTY, CONV_FAIL = 0, 1, 2
 
@@ -308,6 +308,8 @@ def parse(fmt: Format, types, data) -> ParseResult:
                 else:
                     vals = np.zeros(0, np.uint8)
                 cols.append(Column(t, vals, offs, validity, nb))
+            elif t == SKIP:  # a column that is not selected: nothing is kept
+                cols.append(Column(t, np.zeros(0, np.uint8), None, np.zeros(0, np.uint8), 0))
             else:
                 dt = _NP_TYPE[t]
                 width = np.dtype(dt).itemsize

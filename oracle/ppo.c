@@ -321,6 +321,7 @@ typedef struct {
 static void on_data(parse_state* p, uint8_t b) {
   uint32_t c = p->nfields;
   if (c >= p->C) return; /* fields past the schema are dropped */
+  if (p->types[c] == PPO_SKIP) return; /* a column that is not selected */
   if (p->types[c] == PPO_STRING) {
     buf_byte(&p->values[c], b);
     p->bytes_total[c] += 1;
@@ -331,7 +332,7 @@ static void on_data(parse_state* p, uint8_t b) {
 
 static void end_field(parse_state* p) {
   uint32_t c = p->nfields;
-  if (c < p->C) {
+  if (c < p->C && p->types[c] != PPO_SKIP) {
     if (p->types[c] == PPO_STRING) {
       p->field_end[c] = (int64_t)p->values[c].n;
     } else {
@@ -347,9 +348,11 @@ static void end_field(parse_state* p) {
 static void end_record(parse_state* p) {
   int valid = (p->nfields == p->C);
   for (uint32_t c = 0; c < p->C; ++c)
-    if (c < p->nfields && p->types[c] != PPO_STRING && p->field_conv[c] == PPO_CONV_FAIL)
+    if (c < p->nfields && p->types[c] != PPO_STRING && p->types[c] != PPO_SKIP &&
+        p->field_conv[c] == PPO_CONV_FAIL)
       valid = 0;
   for (uint32_t c = 0; c < p->C; ++c) {
+    if (p->types[c] == PPO_SKIP) continue; /* nothing is stored for it */
     int present = c < p->nfields;
     int nonnull = 1;
     if (p->types[c] == PPO_STRING) {

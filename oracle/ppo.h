@@ -46,7 +46,8 @@ enum {
   PPO_FLOAT64 = 3,
   PPO_TIMESTAMP_S = 4,  /* YYYY-MM-DD[ T]hh:mm:ss -> int64 seconds, UTC */
   PPO_DATE_D = 5,       /* YYYY-MM-DD -> int32 days since 1970-01-01 */
-  PPO_TIMESTAMP_CLF = 6 /* dd/Mon/yyyy:hh:mm:ss +hhmm -> int64 seconds, UTC */
+  PPO_TIMESTAMP_CLF = 6, /* dd/Mon/yyyy:hh:mm:ss +hhmm -> int64 seconds, UTC */
+  PPO_SKIP = 7           /* Sec. 4.3, selecting columns: the field counts, nothing is kept */
 };
 
 enum {

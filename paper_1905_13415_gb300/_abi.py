@@ -14,9 +14,9 @@ OK = 0
 E_ARG, E_NOMEM, E_CUDA, E_INVALID_INPUT, E_UNTERMINATED = -1, -2, -3, -4, -5
 E_CAPACITY, E_TIMEOUT, E_BAD_TABLE, E_UNSUPPORTED = -6, -7, -8, -9
 
-STRING, INT32, INT64, FLOAT64, TIMESTAMP_S, DATE_D, TIMESTAMP_CLF = range(7)
+STRING, INT32, INT64, FLOAT64, TIMESTAMP_S, DATE_D, TIMESTAMP_CLF, SKIP = range(8)
 TYPE_NAMES = {"string": STRING, "int32": INT32, "int64": INT64, "float64": FLOAT64,
-              "timestamp": TIMESTAMP_S, "date": DATE_D, "timestamp_clf": TIMESTAMP_CLF}
+              "timestamp": TIMESTAMP_S, "date": DATE_D, "timestamp_clf": TIMESTAMP_CLF, "skip": SKIP}
 
 OPT_TILE_CONFIG, OPT_TIMEOUT_MS, OPT_GRID_LIMIT, OPT_PARTIAL_INPUT, OPT_FIRST_ITEM = 1, 2, 3, 4, 5
 

@@ -102,7 +102,7 @@ __global__ void pp_finalize_kernel(const __grid_constant__ Launch L) {
       for (uint32_t c = 0; c < TB.num_columns; ++c) {
         uint32_t bits = ok;
         if (TB.num_slot[c] != 0xFF) bits &= ~J.null_bits[TB.num_slot[c] * J.bit_words + w];
-        put_bitmap_word(cols[c].validity, w, bits, nbytes);
+        if (cols[c].validity != nullptr) put_bitmap_word(cols[c].validity, w, bits, nbytes);
       }
     }
     for (int off = 16; off > 0; off >>= 1) rej += __shfl_xor_sync(0xffffffffu, rej, off);
@@ -241,6 +241,7 @@ cudaError_t kernel_occupancy(const void* kernel, int threads, size_t smem, int d
 int nspec_of(const Tables& t) { return t.num_symbols <= 4 ? 4 : (t.num_symbols <= 8 ? 8 : 16); }
 
 bool column_ok(const pp_column& c, uint32_t type) {
+  if (type == PP_SKIP) return true;  // nothing is stored for it
   if (c.validity == nullptr || c.values == nullptr) return false;
   if (type == PP_STRING) return c.offsets != nullptr;
   return true;
@@ -465,7 +466,7 @@ extern "C" pp_status parparaw_create(const pp_dfa* dfa, const pp_symbol_groups* 
   uint32_t ns = 0, nn = 0;
   for (uint32_t c = 0; c < schema->num_columns; ++c) {
     const uint32_t ty = schema->types[c];
-    if (ty > PP_TIMESTAMP_CLF) { delete P; return PP_E_BAD_TABLE; }
+    if (ty > PP_SKIP) { delete P; return PP_E_BAD_TABLE; }
     P->types[c] = ty;
     T.col_type[c] = static_cast<uint8_t>(ty);
     T.str_slot[c] = 0xFF;
@@ -473,7 +474,7 @@ extern "C" pp_status parparaw_create(const pp_dfa* dfa, const pp_symbol_groups* 
     if (ty == PP_STRING) {
       if (ns >= PP_MAX_STRING_COLUMNS) { delete P; return PP_E_UNSUPPORTED; }
       T.str_slot[c] = static_cast<uint8_t>(ns++);
-    } else {
+    } else if (ty != PP_SKIP) {
       T.num_slot[c] = static_cast<uint8_t>(nn++);
     }
   }

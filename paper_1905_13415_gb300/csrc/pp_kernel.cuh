@@ -1045,7 +1045,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
                 const uint32_t slot = TB.str_slot[c2];
                 if (slot != 0xFF)
                   cols[c2].offsets[row + 1] = H->col_base[slot] + s_cnt[slot * NT + tid];
-                else
+                else if (TB.num_slot[c2] != 0xFF)
                   store_value(cols[c2], TB.col_type[c2], row, 0);
               }
             }

@@ -72,6 +72,11 @@ class Output:
         nbits = (self.rows_cap + 7) // 8
         self.values, self.offsets, self.validity = [], [], []
         for c, t in enumerate(self.types):
+            if t == _abi.SKIP:  # a column that is not selected: no buffers
+                self.values.append(None)
+                self.offsets.append(None)
+                self.validity.append(None)
+                continue
             if t == _abi.STRING:
                 cap = int(values_caps[c])
                 self.values.append(torch.empty(max(cap, 1), dtype=torch.uint8, device=device))
@@ -88,9 +93,9 @@ class Output:
         self.desc.rows_cap = self.rows_cap
         for c in range(len(self.types)):
             col = self.desc.cols[c]
-            col.values = _ptr(self.values[c])
+            col.values = _ptr(self.values[c]) if self.values[c] is not None else None
             col.offsets = _ptr(self.offsets[c]) if self.offsets[c] is not None else None
-            col.validity = _ptr(self.validity[c])
+            col.validity = _ptr(self.validity[c]) if self.validity[c] is not None else None
             col.values_cap = self.values_caps[c]
         self.desc.row_valid = _ptr(self.row_valid)
         self.desc.result = _ptr(self.result_buf)
@@ -98,6 +103,8 @@ class Output:
     def nbytes(self) -> int:
         n = self.row_valid.numel() + self.result_buf.numel()
         for v, o, m in zip(self.values, self.offsets, self.validity):
+            if v is None:
+                continue
             n += v.numel() * v.element_size() + m.numel()
             if o is not None:
                 n += o.numel() * 8
@@ -117,6 +124,8 @@ class Output:
         nb = (rows + 7) // 8
         n = nb
         for c, t in enumerate(self.types):
+            if t == _abi.SKIP:
+                continue
             if t == _abi.STRING:
                 n += res.values_bytes_needed[c] + 8 * (rows + 1)
             else:
@@ -131,6 +140,9 @@ class Output:
         nb = (rows + 7) // 8
         cols = []
         for c, t in enumerate(self.types):
+            if t == _abi.SKIP:
+                cols.append({"type": t, "values": None, "offsets": None, "validity": None})
+                continue
             validity = self.validity[c][:nb].cpu().numpy()
             if t == _abi.STRING:
                 offs = self.offsets[c][: rows + 1].cpu().numpy()

@@ -20,6 +20,7 @@ import time
 import numpy as np
 import torch
 
+from . import _abi
 from .parser import Output, Parser, parse_batch
 
 
@@ -38,7 +39,9 @@ class Request:
         rows = self.rows_cap
         n = 2 * ((rows + 7) // 8) + 1024
         for t, cap in zip(self.parser.types, self.values_caps):
-            n += (cap + 8 * (rows + 1)) if t == 0 else 8 * rows
+            if t == _abi.SKIP:  # a column that is not selected holds nothing
+                continue
+            n += (cap + 8 * (rows + 1)) if t == _abi.STRING else 8 * rows
             n += (rows + 7) // 8
         return n
 

@@ -64,6 +64,9 @@ class StreamParser:
         with torch.cuda.stream(self.s_d2h):
             for c, t in enumerate(out.types):
                 col = {}
+                if t == _abi.SKIP:  # not selected: nothing to copy
+                    cols.append({"values": None, "offsets": None, "validity": None})
+                    continue
                 if t == _abi.STRING:
                     nbytes = int(res.values_bytes_needed[c])
                     col["values"] = _host_like(out.values[c], nbytes)

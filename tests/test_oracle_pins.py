@@ -341,3 +341,17 @@ def test_inference_agrees_with_the_schema_and_the_parse(workload):
     assert O.parse(fmt, types, raw).n_rejected == 0
     if workload == "trip":  # columns the generator writes as small integers and 2-decimal floats
         assert types[0] == O.INT32 and types[4] == O.FLOAT64 and types[1] == O.STRING
+
+
+def test_skipped_columns_count_but_keep_nothing():
+    # Sec. 4.3, selecting columns: a skipped column's fields still count for
+    # the record's field count; every other column is as if it were kept
+    raw = b'1,xx,a\n2,"y,y",b\n3\n4,zz,c,9\n5,,d\n'
+    full = O.parse(O.csv6(), [O.INT32, O.STRING, O.STRING], raw)
+    skip = O.parse(O.csv6(), [O.INT32, O.SKIP, O.STRING], raw)
+    assert (skip.rows, skip.n_rejected) == (full.rows, full.n_rejected) == (5, 2)
+    assert skip.columns[1].values.size == 0 and skip.columns[1].bytes_total == 0
+    for c in (0, 2):
+        assert np.array_equal(skip.columns[c].validity, full.columns[c].validity)
+        assert [skip.field(r, c) for r in range(5)] == [full.field(r, c) for r in range(5)]
+    assert np.array_equal(skip.row_valid, full.row_valid)
