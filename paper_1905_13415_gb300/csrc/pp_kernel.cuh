@@ -476,6 +476,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       H->tile_last_rd = 0;
       H->eof_rd = 0;
     }
+    if (tid < PP_MAX_STRING_COLUMNS) H->round_base[tid] = 0;
     __syncthreads();
     const unsigned long long item = H->item;
     if (item >= L.total_tiles) break;
@@ -790,8 +791,16 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     // [15] it ends a record, [23:16] its column (saturated), [24] open field.
     // s_rec[k] = first entry of the round's k-th record.  The thread that
     // writes the round's last entry leaves the next round's starting point.
-    auto build_round = [&](uint32_t f0, uint32_t f1) {
-      const uint32_t rr0 = H->rr0;
+    // The start of a round: the end of its field f0 - 1 (the tile's data start
+    // - 1 for f0 = 0) and the record of field f0.  Round 0 starts at the
+    // tile's start; later rounds read what the previous round left in H.
+    struct RoundStart {
+      int prev_pos;
+      uint32_t rr0;
+    };
+    const RoundStart first_round{P0 - 1, 0u};
+    auto build_round = [&](uint32_t f0, uint32_t f1, RoundStart r0) {
+      const uint32_t rr0 = r0.rr0;
       if (tid == 0) s_rec[0] = 0;
       if (dl_ex < f1 && dl_ex + ndl > f0) {
         uint32_t g = dl_ex, c = col_start, rr = row_start;
@@ -830,11 +839,11 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     // Per-slot string bytes of the round's fields; each thread takes an
     // equal share of consecutive entries.  Leaves the exclusive per-thread
     // sums in s_cnt and the round totals in round_tot.
-    auto count_round = [&](uint32_t nwin) {
+    auto count_round = [&](uint32_t nwin, RoundStart r0) {
       const uint32_t per = (nwin + NT - 1) / NT;
       const uint32_t b0 = min(tid * per, nwin), b1 = min(b0 + per, nwin);
       for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
-      uint32_t dprev = data_before(b0 == 0 ? H->prev_pos + 1 : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu));
+      uint32_t dprev = data_before(b0 == 0 ? r0.prev_pos + 1 : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu));
       for (uint32_t g = b0; g < b1; ++g) {
         const uint32_t fe = s_fe[g];
         const uint32_t de = data_before(static_cast<int>(fe & 0x7FFFu));
@@ -881,13 +890,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       __syncwarp();
     };
 
-    auto start_rounds = [&]() {
-      if (tid == 0) {
-        H->prev_pos = P0 - 1;
-        H->rr0 = 0;
-      }
-      if (tid < PP_MAX_STRING_COLUMNS) H->round_base[tid] = 0;
-      __syncthreads();
+    auto round_start = [&](uint32_t r) -> RoundStart {  // after next_round's barrier for r > 0
+      return r == 0 ? first_round : RoundStart{H->prev_pos, H->rr0};
     };
     auto next_round = [&]() {  // after a barrier that follows the round's last use of its list
       if (tid == 0) {
@@ -900,12 +904,11 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
 
     // ------------------------ pass 1: string bytes per column + chain 3
     if (NS > 0) {
-      start_rounds();
       for (uint32_t r = 0; r < nrounds; ++r) {
         const uint32_t f0 = r * FCAP, f1 = min(f0 + FCAP, NF);
-        build_round(f0, f1);
+        build_round(f0, f1, round_start(r));
         PP_PHASE(13);
-        count_round(f1 - f0);
+        count_round(f1 - f0, round_start(r));
         if (r + 1 < nrounds) next_round();
       }
       if (tid < static_cast<int>(NS)) H->tile_tot[tid] = H->round_base[tid] + H->round_tot[tid];
@@ -967,17 +970,21 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     };
 
     // ------------------------------------------- pass 2: emit, by rounds
-    if (NS == 0 || nrounds > 1) start_rounds();  // else pass 1's only round is still in place
+    if (NS > 0 && nrounds > 1) {  // the rounds again from the first (else pass 1's only round is in place)
+      if (tid < static_cast<int>(NS)) H->round_base[tid] = 0;
+      __syncthreads();
+    }
     for (uint32_t r = 0; r < nrounds; ++r) {
       const uint32_t f0 = r * FCAP, f1 = min(f0 + FCAP, NF), nwin = f1 - f0;
+      const RoundStart rs = round_start(r);
       if (NS == 0 || nrounds > 1) {
-        build_round(f0, f1);
-        if (NS > 0) count_round(nwin);
+        build_round(f0, f1, rs);
+        if (NS > 0) count_round(nwin, rs);
         PP_PHASE(14);
       }
-      const uint32_t rr0 = H->rr0;
+      const uint32_t rr0 = rs.rr0;
       const uint32_t nrec_win = H->rr_last - rr0 + 1;
-      const int prev_pos = H->prev_pos;
+      const int prev_pos = rs.prev_pos;
 
       // (1) equal shares of consecutive entries: per-slot running byte
       // positions -> s_fo (field end minus data bytes before it, mod 2^16);
