@@ -68,6 +68,16 @@ struct TileShape {
   static_assert(T < 32768, "tile positions are 15-bit field-list entries");
 };
 
+// A long string field queued for a warp-wide copy: destination, first data
+// byte and end in the tile, data bytes, whether they are contiguous.
+struct LongField {
+  uint8_t* dst;
+  uint16_t fd, e;
+  uint32_t nb;
+  uint32_t contiguous;
+};
+constexpr uint32_t kLongQ = 64;  // long fields queued per round (more are copied where found)
+
 struct SmemHead {
   uint64_t mbar;
   unsigned long long item;
@@ -93,6 +103,8 @@ struct SmemHead {
   uint32_t rr_next;
   uint32_t round_tot[PP_MAX_STRING_COLUMNS];   // string bytes of the round per slot
   uint32_t round_base[PP_MAX_STRING_COLUMNS];  // string bytes of the earlier rounds
+  uint32_t nlong;
+  LongField longs[kLongQ];
 #ifdef PP_PHASE_TIMING
   long long ph_cycles[16];  // profiling builds only
 #endif
@@ -475,6 +487,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       H->job = j;
       H->tile_last_rd = 0;
       H->eof_rd = 0;
+      H->nlong = 0;
     }
     if (tid < PP_MAX_STRING_COLUMNS) H->round_base[tid] = 0;
     __syncthreads();
@@ -897,6 +910,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       if (tid == 0) {
         H->prev_pos = H->next_prev_pos;
         H->rr0 = H->rr_next;
+        H->nlong = 0;
       }
       if (tid < static_cast<int>(NS)) H->round_base[tid] += H->round_tot[tid];
       __syncthreads();
@@ -1022,8 +1036,14 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
                   gdst = static_cast<uint8_t*>(cols[c].values) + off;
                   fd = first_data(eprev + 1, e);
                   contiguous = data_before(fd + static_cast<int>(nb)) == dprev + nb;
-                  if (nb > kLongField) {
-                    is_long = true;
+                  if (nb > kLongField) {  // queued for any warp, else copied by this warp below
+                    const uint32_t q = atomicAdd(&H->nlong, 1u);
+                    if (q < kLongQ) {
+                      H->longs[q] = LongField{gdst, static_cast<uint16_t>(fd), static_cast<uint16_t>(e), nb,
+                                              contiguous ? 1u : 0u};
+                    } else {
+                      is_long = true;
+                    }
                   } else if (contiguous) {
                     smem_copy(gdst, s_tile + fd, static_cast<int>(nb));
                   } else {
@@ -1089,6 +1109,25 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       }
       __syncthreads();
       PP_PHASE(10);
+      // the queued long fields, a warp each, spread over all warps
+      for (uint32_t i = warp, nl = min(H->nlong, kLongQ); i < nl; i += Shape::NW) {
+        const LongField lf = H->longs[i];
+        if (lf.contiguous) {
+          warp_copy_out(lf.dst, s_tile + lf.fd, static_cast<int>(lf.nb), lane);
+        } else {  // data bytes with gaps: each lane places the bytes it holds by their rank
+          const uint32_t d0 = data_before(lf.fd);
+          for (int u = lf.fd / B; u * B < lf.e; ++u) {
+            for (int x = u * B + lane; x < (u + 1) * B; x += 32) {
+              if (x < lf.fd || x >= lf.e) continue;
+              const int ix = x - u * B;
+              if ((s_dm[u * MW + (ix >> 6)] >> (ix & 63)) & 1ull) {
+                const uint32_t rank = data_before(x) - d0;
+                if (rank < lf.nb) lf.dst[rank] = s_tile[x];
+              }
+            }
+          }
+        }
+      }
 
       // (2) string offsets and numeric conversions, record by record: G
       // threads per record take every G-th field (G = 1 when records are
