@@ -16,14 +16,22 @@
 //           look-back over the tiles' status words (chain 1).
 //   a4      re-simulation from the chunk's start state emitting the data /
 //           field / record / control tags as bit masks (Sec. 3.1).
-//   a5      record counts (popcount) and absolute/relative column offsets
-//           (Sec. 3.2): block scan + look-back (chain 2).  Then the bytes
-//           every string column receives: block scan + look-back (chain 3).
-//   a6      stable partition: each string field's data bytes are gathered
-//           in shared memory in column order and written with TMA bulk
-//           stores; Arrow int64 offsets are written at field ends (Sec. 3.3).
-//   a7      numeric fields are converted by the thread holding the
-//           delimiter that opens them (Sec. 3.3).
+//   a5      record counts (popcount), absolute/relative column offsets, data
+//           bytes and delimiters per chunk (Sec. 3.2): one block scan, then
+//           look-back (chain 2) for the tile's first record and column.
+//           The field list: every delimiter of the tile (and the open field
+//           after the last one) becomes an entry with its end, column and
+//           record; per-column string bytes summed over equal shares of the
+//           entries, block-scanned, then look-back (chain 3) for each
+//           column's output base.  Tiles with more fields than the list
+//           holds are processed in rounds.
+//   a6      stable partition (Sec. 3.3): over equal shares of the entries,
+//           each string field's running offset and its data bytes straight
+//           from the tile to the column (long fields queued and copied by
+//           whole warps, 16-byte stores); Arrow int64 offsets per record.
+//   a7      numeric fields are converted one record per thread (or several
+//           threads per record when the tile holds few records), column by
+//           column (Sec. 3.3).
 //   a8      invalid transitions, field-count mismatches and conversion
 //           failures are recorded; the finalize kernel turns them into
 //           validity bitmaps and the result.

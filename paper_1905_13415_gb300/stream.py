@@ -32,8 +32,27 @@ class Partition:
     row_valid: torch.Tensor
 
 
-def _host_like(t: torch.Tensor, n: int) -> torch.Tensor:
-    return torch.empty(max(n, 1), dtype=t.dtype, pin_memory=True)
+class HostArena:
+    """One pinned host buffer that the columns of a stream's partitions are
+    carved from, so that a parse allocates no pinned memory per partition.
+    Reusable across parses: the partitions of a parse stay valid until the
+    arena's next parse (reset)."""
+
+    def __init__(self, nbytes: int):
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=True)
+        self.used = 0
+
+    def reset(self) -> None:
+        self.used = 0
+
+    def take(self, n: int, dtype) -> torch.Tensor | None:
+        size = torch.empty(0, dtype=dtype).element_size()
+        start = (self.used + 63) & ~63
+        end = start + max(n, 1) * size
+        if end > self.buf.numel():
+            return None
+        self.used = end
+        return self.buf[start:end].view(dtype)
 
 
 class StreamParser:
@@ -49,6 +68,7 @@ class StreamParser:
         self.s_parse = torch.cuda.Stream(device=self.device)
         self.s_d2h = torch.cuda.Stream(device=self.device)
         self.outs = [None, None]
+        self.arena = None
 
     def _out(self, b: int) -> Output:
         if self.outs[b] is None:
@@ -57,7 +77,15 @@ class StreamParser:
             self.outs[b] = self.parser.allocate(rows, [nbytes] * len(self.parser.types), device=self.device)
         return self.outs[b]
 
+    def _host_like(self, t: torch.Tensor, n: int) -> torch.Tensor:
+        if self.arena is not None:
+            x = self.arena.take(n, t.dtype)
+            if x is not None:
+                return x
+        return torch.empty(max(n, 1), dtype=t.dtype, pin_memory=True)
+
     def _copy_back(self, out: Output, res, nbytes_in: int, done: torch.cuda.Event) -> Partition:
+        _host_like = self._host_like
         rows = res.rows
         nb = (rows + 7) // 8
         cols = []
@@ -84,8 +112,13 @@ class StreamParser:
             done.record(self.s_d2h)
         return Partition(rows, nbytes_in, cols, rv)
 
-    def parse(self, host: torch.Tensor) -> list[Partition]:
-        """Parses the pinned uint8 host tensor; returns the partitions' columns."""
+    def parse(self, host: torch.Tensor, arena: HostArena | None = None) -> list[Partition]:
+        """Parses the pinned uint8 host tensor; returns the partitions' columns,
+        in pinned host memory (carved from `arena` when given: then they stay
+        valid until the arena's next use)."""
+        self.arena = arena
+        if arena is not None:
+            arena.reset()
         n = host.numel()
         nparts = max(1, (n + self.part - 1) // self.part)
         ev = lambda: torch.cuda.Event()  # noqa: E731

@@ -124,8 +124,11 @@ def test_streamed_parse_equals_whole_parse(pp, workload):
     schema, dialect = synth.SCHEMAS[workload], synth.DIALECT[workload]
     ref = oracle_parse(dialect, schema, raw)
     p = pp.Parser(pp.formats.by_name(dialect), schema, tile_config=2)
+    from paper_1905_13415_gb300.stream import HostArena
+
     host = torch.frombuffer(bytearray(raw), dtype=torch.uint8).pin_memory()
-    parts = StreamParser(p, partition_bytes=37_000, carry_bytes=64_000).parse(host)
+    sp = StreamParser(p, partition_bytes=37_000, carry_bytes=64_000)
+    parts = sp.parse(host, HostArena(3 * len(raw) + (1 << 20)) if workload == "mixed" else None)
     assert len(parts) > 3
     assert sum(x.rows for x in parts) == ref.rows
     for c, col in enumerate(ref.columns):
