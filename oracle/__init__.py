@@ -98,6 +98,10 @@ def lib():
                                 ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t,
                                 ctypes.POINTER(_Result)]
         L.ppo_parse.restype = ctypes.c_int
+        L.ppo_parse_skip.argtypes = [ctypes.POINTER(_Format), ctypes.POINTER(ctypes.c_uint32),
+                                     ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
+                                     ctypes.POINTER(_Result)]
+        L.ppo_parse_skip.restype = ctypes.c_int
         L.ppo_free.argtypes = [ctypes.POINTER(_Result)]
         L.ppo_convert.argtypes = [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
         L.ppo_convert.restype = ctypes.c_int
@@ -285,12 +289,12 @@ class ParseResult:
         return bool((self.columns[c].validity[r >> 3] >> (r & 7)) & 1)
 
 
-def parse(fmt: Format, types, data) -> ParseResult:
+def parse(fmt: Format, types, data, skip_records: int = 0) -> ParseResult:
     types_arr = (ctypes.c_uint32 * len(types))(*types)
     buf = np.frombuffer(data, dtype=np.uint8) if not isinstance(data, np.ndarray) else data
     res = _Result()
-    rc = lib().ppo_parse(ctypes.byref(fmt._c), types_arr, len(types), buf.ctypes.data, len(buf),
-                         ctypes.byref(res))
+    rc = lib().ppo_parse_skip(ctypes.byref(fmt._c), types_arr, len(types), buf.ctypes.data, len(buf),
+                              skip_records, ctypes.byref(res))
     if rc != 0:
         raise ValueError("bad schema")
     try:

@@ -316,9 +316,11 @@ typedef struct {
   uint8_t field_conv[PPO_MAX_COLUMNS];           /* numeric: PPO_CONV_* of field c */
   uint64_t field_value[PPO_MAX_COLUMNS];
   int64_t rows, rejected;
+  uint64_t skip, seen;                           /* records to skip (Sec. 4.3), records ended */
 } parse_state;
 
 static void on_data(parse_state* p, uint8_t b) {
+  if (p->seen < p->skip) return; /* a skipped record keeps nothing */
   uint32_t c = p->nfields;
   if (c >= p->C) return; /* fields past the schema are dropped */
   if (p->types[c] == PPO_SKIP) return; /* a column that is not selected */
@@ -332,7 +334,7 @@ static void on_data(parse_state* p, uint8_t b) {
 
 static void end_field(parse_state* p) {
   uint32_t c = p->nfields;
-  if (c < p->C && p->types[c] != PPO_SKIP) {
+  if (c < p->C && p->types[c] != PPO_SKIP && p->seen >= p->skip) {
     if (p->types[c] == PPO_STRING) {
       p->field_end[c] = (int64_t)p->values[c].n;
     } else {
@@ -346,6 +348,13 @@ static void end_field(parse_state* p) {
 }
 
 static void end_record(parse_state* p) {
+  if (p->seen < p->skip) { /* Sec. 4.3, skipping records: it leaves no row */
+    p->seen += 1;
+    p->nfields = 0;
+    p->num_len = 0;
+    return;
+  }
+  p->seen += 1;
   int valid = (p->nfields == p->C);
   for (uint32_t c = 0; c < p->C; ++c)
     if (c < p->nfields && p->types[c] != PPO_STRING && p->types[c] != PPO_SKIP &&
@@ -375,9 +384,15 @@ static void end_record(parse_state* p) {
 
 int ppo_parse(const ppo_format* f, const uint32_t* types, uint32_t C, const uint8_t* in,
               size_t len, ppo_result* out) {
+  return ppo_parse_skip(f, types, C, in, len, 0, out);
+}
+
+int ppo_parse_skip(const ppo_format* f, const uint32_t* types, uint32_t C, const uint8_t* in,
+                   size_t len, uint64_t skip_records, ppo_result* out) {
   memset(out, 0, sizeof(*out));
   if (C == 0 || C > PPO_MAX_COLUMNS) return -1;
   parse_state* p = (parse_state*)calloc(1, sizeof(parse_state));
+  p->skip = skip_records;
   p->f = f;
   p->types = types;
   p->C = C;

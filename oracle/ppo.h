@@ -111,6 +111,12 @@ int ppo_parse(const ppo_format* f, const uint32_t* types, uint32_t num_columns,
               const uint8_t* in, size_t len, ppo_result* out);
 void ppo_free(ppo_result* r);
 
+/* The same parse with the first skip_records records skipped (Sec. 4.3,
+ * skipping records): they are recognised but leave no row, no bytes, no
+ * conversion and no reject; rows count from the next record. */
+int ppo_parse_skip(const ppo_format* f, const uint32_t* types, uint32_t num_columns,
+                   const uint8_t* in, size_t len, uint64_t skip_records, ppo_result* out);
+
 /* Type conversion of one field's data bytes (Sec. 3.3). *out receives an
  * int32/int64/double bit pattern in its low bytes. Returns PPO_CONV_*. */
 int ppo_convert(uint32_t type, const uint8_t* text, size_t len, void* out);

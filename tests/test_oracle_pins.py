@@ -355,3 +355,58 @@ def test_skipped_columns_count_but_keep_nothing():
         assert np.array_equal(skip.columns[c].validity, full.columns[c].validity)
         assert [skip.field(r, c) for r in range(5)] == [full.field(r, c) for r in range(5)]
     assert np.array_equal(skip.row_valid, full.row_valid)
+
+
+@pytest.mark.parametrize("workload,n", [("mixed", 400), ("trip", 300), ("review", 40), ("log", 300)])
+def test_skipped_records_equal_the_input_without_them(workload, n):
+    # Sec. 4.3, skipping records: skipping the first k records gives what
+    # parsing the input with those records' bytes cut off gives (each record
+    # ends in the start state, so the cut loses no context)
+    raw, _ = synth.records(workload, synth.BASE_SEED + 5, 0, n)
+    dialect = synth.DIALECT[workload]
+    fmt = O.csv6() if dialect == "csv" else O.log8()
+    types = [_OTYPE[t] for t in synth.SCHEMAS[workload]]
+    for k in (0, 1, 5, n - 1, n, n + 3):
+        cut = _record_start(raw, dialect, k)
+        a = O.parse(fmt, types, raw, skip_records=k)
+        b = O.parse(fmt, types, raw[cut:])
+        assert a.rows == max(n - k, 0)
+        assert (a.rows, a.n_rejected, a.status) == (b.rows, b.n_rejected, b.status), k
+        for c in range(len(types)):
+            assert np.array_equal(a.columns[c].validity, b.columns[c].validity), (k, c)
+            assert a.columns[c].bytes_total == b.columns[c].bytes_total, (k, c)
+            assert [a.field(r, c) for r in range(a.rows)] == [b.field(r, c) for r in range(b.rows)], (k, c)
+        assert np.array_equal(a.row_valid, b.row_valid), k
+
+
+def _record_start(raw: bytes, dialect: str, n: int) -> int:
+    """Byte offset where record n starts, found by a quote-aware scan written
+    apart from the oracle (CSV: a newline outside double quotes ends a record;
+    the web log: a newline outside quotes and brackets)."""
+    quoted = bracket = False
+    seen = 0
+    if n == 0:
+        return 0
+    for i, ch in enumerate(raw):
+        if ch == 0x22:
+            quoted = not quoted
+        elif dialect != "csv" and not quoted and ch in (0x5B, 0x5D):
+            bracket = ch == 0x5B
+        elif ch == 0x0A and not quoted and not bracket:
+            seen += 1
+            if seen == n:
+                return i + 1
+    return len(raw)
+
+
+def test_skipped_records_leave_no_rejects_and_keep_validation():
+    # a malformed record that is skipped is not rejected, while an invalid
+    # byte inside a skipped record still fails the input
+    raw = b'1\n2,b\n3,c\n'
+    assert O.parse(O.csv6(), [O.INT32, O.STRING], raw).n_rejected == 1
+    s = O.parse(O.csv6(), [O.INT32, O.STRING], raw, skip_records=1)
+    assert (s.rows, s.n_rejected) == (2, 0) and s.field(0, 1) == b'b'
+    bad = b'1,"x"y\n2,b\n'
+    a = O.parse(O.csv6(), [O.INT32, O.STRING], bad)
+    b = O.parse(O.csv6(), [O.INT32, O.STRING], bad, skip_records=1)
+    assert a.status == b.status != 0 and a.first_invalid_offset == b.first_invalid_offset
