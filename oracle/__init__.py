@@ -108,6 +108,9 @@ def lib():
         L.ppo_infer.argtypes = [ctypes.POINTER(_Format), ctypes.c_void_p, ctypes.c_size_t,
                                 ctypes.POINTER(_Inference)]
         L.ppo_infer.restype = ctypes.c_int
+        L.ppo_infer_skip.argtypes = [ctypes.POINTER(_Format), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
+                                     ctypes.POINTER(_Inference)]
+        L.ppo_infer_skip.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -340,9 +343,11 @@ class Inference:
     types: list  # per field position: INT32 / INT64 / FLOAT64 / STRING, or NO_TYPE
 
 
-def infer(fmt: Format, data) -> Inference:
-    """Sec. 4.3: column-count and numeric type inference (see ppo_infer)."""
+def infer(fmt: Format, data, skip_records: int = 0) -> Inference:
+    """Sec. 4.3: column-count and numeric type inference (see ppo_infer),
+    over all but the first ``skip_records`` records."""
     buf = np.frombuffer(data, dtype=np.uint8) if not isinstance(data, np.ndarray) else data
     r = _Inference()
-    lib().ppo_infer(ctypes.byref(fmt._c), buf.ctypes.data, len(buf), ctypes.byref(r))
+    lib().ppo_infer_skip(ctypes.byref(fmt._c), buf.ctypes.data, len(buf), ctypes.c_uint64(skip_records),
+                         ctypes.byref(r))
     return Inference(r.status, r.min_fields, r.max_fields, r.records, r.first_invalid_offset, list(r.type))

@@ -476,11 +476,17 @@ static int infer_rank(const uint8_t* text, size_t len) {
 }
 
 int ppo_infer(const ppo_format* f, const uint8_t* in, size_t len, ppo_inference* out) {
+  return ppo_infer_skip(f, in, len, 0, out);
+}
+
+int ppo_infer_skip(const ppo_format* f, const uint8_t* in, size_t len, uint64_t skip_records,
+                   ppo_inference* out) {
   static const uint8_t type_of_rank[5] = {PPO_NO_TYPE, PPO_INT32, PPO_INT64, PPO_FLOAT64, PPO_STRING};
   int rank[PPO_MAX_COLUMNS] = {0};
   uint8_t text[PPO_NUMERIC_MAX_LEN + 1];
   size_t tlen = 0;       /* data bytes of the current field (only the first ones are kept) */
   uint32_t field = 0;    /* position of the current field in its record */
+  uint64_t ended = 0;    /* records ended so far, skipped ones included */
   memset(out, 0, sizeof(*out));
   out->min_fields = 0xFFFFFFFFu;
   int64_t first_invalid = -1;
@@ -489,7 +495,7 @@ int ppo_infer(const ppo_format* f, const uint8_t* in, size_t len, ppo_inference*
   /* a field ends: its narrowest type widens its position's type */
   #define END_FIELD()                                                   \
     do {                                                                \
-      if (field < PPO_MAX_COLUMNS && tlen > 0) {                        \
+      if (ended >= skip_records && field < PPO_MAX_COLUMNS && tlen > 0) { \
         const int r = infer_rank(text, tlen);                           \
         if (r > rank[field]) rank[field] = r;                           \
       }                                                                 \
@@ -498,6 +504,7 @@ int ppo_infer(const ppo_format* f, const uint8_t* in, size_t len, ppo_inference*
   /* a record ends with field + 1 fields */
   #define END_RECORD()                                                  \
     do {                                                                \
+      if (ended++ < skip_records) { field = 0; break; }                 \
       uint32_t n = field + 1 < PPO_INFER_MAX_FIELDS ? field + 1 : PPO_INFER_MAX_FIELDS; \
       if (n < out->min_fields) out->min_fields = n;                     \
       if (n > out->max_fields) out->max_fields = n;                     \

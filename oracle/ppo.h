@@ -139,6 +139,8 @@ typedef struct ppo_inference {
   uint8_t type[PPO_MAX_COLUMNS];
 } ppo_inference;
 int ppo_infer(const ppo_format* f, const uint8_t* in, size_t len, ppo_inference* out);
+int ppo_infer_skip(const ppo_format* f, const uint8_t* in, size_t len, uint64_t skip_records,
+                   ppo_inference* out);  /* ppo_infer over all but the first skip_records records */
 
 #ifdef __cplusplus
 }

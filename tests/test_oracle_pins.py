@@ -410,3 +410,18 @@ def test_skipped_records_leave_no_rejects_and_keep_validation():
     a = O.parse(O.csv6(), [O.INT32, O.STRING], bad)
     b = O.parse(O.csv6(), [O.INT32, O.STRING], bad, skip_records=1)
     assert a.status == b.status != 0 and a.first_invalid_offset == b.first_invalid_offset
+
+
+def test_inference_skips_a_header_record():
+    # a header row makes every column a string; skipped (Sec. 4.3), the
+    # types are those of the body, as if the header were cut off
+    body = b'1,a,2.5\n70000000000,"b,c",3\n,d,-1000.5\n'
+    raw = b'id,name,score\n' + body
+    s = O.infer(O.csv6(), raw)
+    assert s.types[:3] == [O.STRING] * 3 and s.records == 4
+    k = O.infer(O.csv6(), raw, skip_records=1)
+    b = O.infer(O.csv6(), body)
+    assert k.types[:3] == [O.INT64, O.STRING, O.FLOAT64] and k.records == 3
+    assert (k.types, k.records, k.min_fields, k.max_fields, k.status) == \
+        (b.types, b.records, b.min_fields, b.max_fields, b.status)
+    assert O.infer(O.csv6(), raw, skip_records=9).records == 0
