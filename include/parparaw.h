@@ -191,11 +191,17 @@ typedef enum pp_option {
                                delimiter are an incomplete record, not emitted
                                and not an error; result.consumed reports where
                                they start.  0 (default) = the input is whole. */
-  PP_OPT_FIRST_ITEM = 5     /* testing only: the work queue starts at this tile
+  PP_OPT_FIRST_ITEM = 5,    /* testing only: the work queue starts at this tile
                                (default 0).  The tiles before it never run, so
                                later tiles' bounded look-back waits expire and
                                the parse reports PP_E_TIMEOUT; the context stays
                                usable.  Outputs of such a parse are undefined. */
+  PP_OPT_SKIP_RECORDS = 6   /* skipping records (Sec. 4.3): the first n records
+                               (0 <= n < 2^32, default 0), e.g. a header, are
+                               recognised and validated but leave no row, no
+                               string bytes, no conversion and no reject; row 0
+                               is record n.  result.rows counts the rows left.
+                               parparaw_infer skips them too. */
 } pp_option;
 
 typedef struct pp_parser_info {

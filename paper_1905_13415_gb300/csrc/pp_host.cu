@@ -509,6 +509,10 @@ extern "C" pp_status parparaw_set_option(pp_parser* P, pp_option option, int64_t
       if (value < 0 || value > 0xFFFFFFFFll) return PP_E_ARG;
       P->first_item = static_cast<uint32_t>(value);
       return PP_OK;
+    case PP_OPT_SKIP_RECORDS:
+      if (value < 0 || value > 0xFFFFFFFFll) return PP_E_ARG;
+      P->tab.skip_records = static_cast<uint32_t>(value);
+      return PP_OK;
     default:
       return PP_E_ARG;
   }

@@ -758,7 +758,14 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     }
     __syncthreads();
     PP_PHASE(5);
-    const uint64_t tile_row0 = H->prefix_rc & kRecMask;
+    // Skipping records (Sec. 4.3): record i of the input (from 0) leaves row
+    // i - S, and nothing at all for i < S.  The tile's first record is
+    // record tile_rec0, row row0 (mod 2^64); its first skip_tile records
+    // are skipped.
+    const uint64_t tile_rec0 = H->prefix_rc & kRecMask;
+    const uint64_t row0 = tile_rec0 - TB.skip_records;
+    const uint32_t skip_tile =
+        TB.skip_records > tile_rec0 ? static_cast<uint32_t>(TB.skip_records - tile_rec0) : 0u;
     const uint32_t tile_col0 = static_cast<uint32_t>((H->prefix_rc >> 40) & 0x1FFFFF);
     const uint32_t row_start = rc_ex & 0xFFFFu;  // relative to the tile's first record
     const uint32_t col_start = (rc_ex >> 31) ? ((rc_ex >> 16) & kColSat)
@@ -820,6 +827,13 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       uint32_t rr0;
     };
     const RoundStart first_round{P0 - 1, 0u};
+    // The round's first entry of a kept record (after build_round's
+    // barrier): 0 unless the round starts among the skipped records.
+    auto first_kept = [&](uint32_t rr0, uint32_t nwin) -> uint32_t {
+      if (rr0 >= skip_tile) return 0u;
+      const uint32_t k = skip_tile - rr0;  // skipped records of the round
+      return k <= H->rr_last - rr0 ? s_rec[k] : nwin;
+    };
     auto build_round = [&](uint32_t f0, uint32_t f1, RoundStart r0) {
       const uint32_t rr0 = r0.rr0;
       if (tid == 0) s_rec[0] = 0;
@@ -863,13 +877,14 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     auto count_round = [&](uint32_t nwin, RoundStart r0) {
       const uint32_t per = (nwin + NT - 1) / NT;
       const uint32_t b0 = min(tid * per, nwin), b1 = min(b0 + per, nwin);
+      const uint32_t kept = first_kept(r0.rr0, nwin);
       for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
       uint32_t dprev = data_before(b0 == 0 ? r0.prev_pos + 1 : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu));
       for (uint32_t g = b0; g < b1; ++g) {
         const uint32_t fe = s_fe[g];
         const uint32_t de = data_before(static_cast<int>(fe & 0x7FFFu));
         const uint32_t c = (fe >> 16) & 0xFFu;
-        if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(de - dprev);
+        if (g >= kept && c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(de - dprev);
         dprev = de;
       }
       // block scan of the per-slot counts, two 16-bit slots per word
@@ -1007,6 +1022,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       const uint32_t rr0 = rs.rr0;
       const uint32_t nrec_win = H->rr_last - rr0 + 1;
       const int prev_pos = rs.prev_pos;
+      const uint32_t kept = first_kept(rr0, nwin);
 
       // (1) equal shares of consecutive entries: per-slot running byte
       // positions -> s_fo (field end minus data bytes before it, mod 2^16);
@@ -1031,7 +1047,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           const uint32_t c = (fe >> 16) & 0xFFu;
           if (NS > 0) {
             const uint32_t de = data_before(e);
-            if (c < C && TB.str_slot[c] != 0xFF) {
+            if (g >= kept && c < C && TB.str_slot[c] != 0xFF) {
               const uint32_t slot = TB.str_slot[c];
               const uint16_t run = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (de - dprev));
               s_cnt[slot * NT + tid] = run;
@@ -1065,7 +1081,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
             dprev = de;
           }
           eprev = e;
-          if (!INFER && (fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
+          if (!INFER && g >= kept && (fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
             // the record ends with the wrong number of fields: reject it and
             // give the missing columns their defaults
             uint32_t klo = 0, khi = nrec_win - 1;
@@ -1073,7 +1089,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
               const uint32_t mid = (klo + khi + 1) >> 1;
               if (s_rec[mid] <= g) klo = mid; else khi = mid - 1;
             }
-            const uint64_t row = tile_row0 + rr0 + klo;
+            const uint64_t row = row0 + rr0 + klo;
             if (row < rows_cap) {
               atomicOr(&J.fail_bits[row >> 5], 1u << (row & 31));
               for (uint32_t c2 = c + 1; c2 < C; ++c2) {
@@ -1147,6 +1163,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         // narrowest type of every non-empty field that starts here
         for (uint32_t j = tid; j < nrec_win * G; j += NT) {
           const uint32_t k = j / G, sub = j - k * G;
+          if (rr0 + k < skip_tile) continue;
           const uint32_t gb = s_rec[k], ge = k + 1 < nrec_win ? s_rec[k + 1] : nwin;
           if (sub == 0 && ge > gb) {
             const uint32_t fl = s_fe[ge - 1];
@@ -1210,7 +1227,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       } else
       for (uint32_t j = tid; j < nrec_win * G; j += NT) {
         const uint32_t k = j / G, sub = j - k * G;
-        const uint64_t row = tile_row0 + rr0 + k;
+        if (rr0 + k < skip_tile) continue;
+        const uint64_t row = row0 + rr0 + k;
         if (row >= rows_cap) break;
         const uint32_t gb = s_rec[k], ge = k + 1 < nrec_win ? s_rec[k + 1] : nwin;
         for (uint32_t g = gb + sub; g < ge; g += G) {
@@ -1242,7 +1260,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       if (tid == PP_MAX_COLUMNS + 1 && s_inf[tid]) atomicMax(&J.misc->inf_max_fields, s_inf[tid]);
     }
     if (last_tile && tid == 0) {
-      J.misc->rows = static_cast<int64_t>(tile_row0 + rec_tile + (trailing ? 1u : 0u));  // read by the finalize kernel only
+      const uint32_t recs = rec_tile + (trailing ? 1u : 0u);  // of the tile; rows: read by the finalize kernel only
+      J.misc->rows = recs >= skip_tile ? static_cast<int64_t>(row0 + recs) : 0;
       J.misc->final_state = static_cast<int32_t>(tile_send);
       for (uint32_t k = 0; k < NS; ++k) J.misc->bytes_total[k] = H->col_base[k] + H->tile_tot[k];
       J.misc->done = 1u;

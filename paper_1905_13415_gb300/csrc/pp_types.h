@@ -20,6 +20,7 @@ struct Tables {
   uint8_t start_state, invalid_state, idempotent, num_columns;
   uint8_t num_str, num_num, partial, pad1;  // partial: more input follows
   uint32_t accept_mask;
+  uint32_t skip_records;  // the first n records leave no row (Sec. 4.3)
 };
 
 struct Col {

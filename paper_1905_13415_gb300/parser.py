@@ -159,7 +159,9 @@ class Parser:
     """A validated DFA + symbol groups + schema (parparaw_create)."""
 
     def __init__(self, fmt: Format, schema, tile_config: int = 0, timeout_ms: int | None = None,
-                 grid_limit: int | None = None):
+                 grid_limit: int | None = None, skip_records: int = 0):
+        """``skip_records``: the first n records (a header, say) are
+        recognised but leave no row (Sec. 4.3, skipping records)."""
         self._lib = _abi.load()
         self.format = fmt
         self.types = [_abi.TYPE_NAMES[t] if isinstance(t, str) else int(t) for t in schema]
@@ -179,17 +181,22 @@ class Parser:
         if rc != _abi.OK:
             raise ParparawError(rc, "parparaw_create")
         self.handle = handle
+        self.skip_records = 0
         if tile_config:
             self.set_option(_abi.OPT_TILE_CONFIG, tile_config)
         if timeout_ms:
             self.set_option(_abi.OPT_TIMEOUT_MS, timeout_ms)
         if grid_limit:
             self.set_option(_abi.OPT_GRID_LIMIT, grid_limit)
+        if skip_records:
+            self.set_option(_abi.OPT_SKIP_RECORDS, skip_records)
 
     def set_option(self, option: int, value: int) -> None:
         rc = self._lib.parparaw_set_option(self.handle, option, int(value))
         if rc != _abi.OK:
             raise ParparawError(rc, "parparaw_set_option")
+        if option == _abi.OPT_SKIP_RECORDS:
+            self.skip_records = int(value)
 
     def info(self) -> _abi.pp_parser_info:
         info = _abi.pp_parser_info()

@@ -139,46 +139,53 @@ class StreamParser:
                 h2d_done[b].record(self.s_h2d)
             return ln
 
-        results: list[Partition] = []
-        lens = [0] * nparts
-        lens[0] = h2d(0)
-        prev = None  # (buffer, start, length, Output) of partition k-1
-        for k in range(nparts):
-            b = k % 2
-            last = k + 1 == nparts
-            carry_len = 0
-            if prev is not None:
-                pb, pstart, plen, pout = prev
-                parse_done[pb].synchronize()
-                res = self._checked(pout, pb, pstart, plen, partial=True)
-                results.append(self._copy_back(self.outs[pb], res, plen, d2h_done[pb]))
-                carry_len = plen - res.consumed
-                if carry_len > self.carry:
-                    raise ParparawError(_abi.E_UNSUPPORTED, "a record is longer than the carry-over region")
+        skip = self.parser.skip_records  # Sec. 4.3: they are all in the first partition
+        try:
+            results: list[Partition] = []
+            lens = [0] * nparts
+            lens[0] = h2d(0)
+            prev = None  # (buffer, start, length, Output) of partition k-1
+            for k in range(nparts):
+                b = k % 2
+                last = k + 1 == nparts
+                carry_len = 0
+                if prev is not None:
+                    pb, pstart, plen, pout = prev
+                    parse_done[pb].synchronize()
+                    res = self._checked(pout, pb, pstart, plen, partial=True)
+                    results.append(self._copy_back(self.outs[pb], res, plen, d2h_done[pb]))
+                    if k == 1 and skip and res.rows == 0:
+                        raise ParparawError(_abi.E_UNSUPPORTED, "the skipped records reach past the first partition")
+                    carry_len = plen - res.consumed
+                    if carry_len > self.carry:
+                        raise ParparawError(_abi.E_UNSUPPORTED, "a record is longer than the carry-over region")
+                    self.s_parse.wait_event(h2d_done[b])
+                    if carry_len:
+                        with torch.cuda.stream(self.s_parse):
+                            self.bufs[b][self.carry - carry_len:self.carry].copy_(
+                                self.bufs[pb][pstart + res.consumed:pstart + plen], non_blocking=True)
+                    carry_done.record(self.s_parse)
+                start = self.carry - carry_len
+                length = carry_len + lens[k]
                 self.s_parse.wait_event(h2d_done[b])
-                if carry_len:
-                    with torch.cuda.stream(self.s_parse):
-                        self.bufs[b][self.carry - carry_len:self.carry].copy_(
-                            self.bufs[pb][pstart + res.consumed:pstart + plen], non_blocking=True)
-                carry_done.record(self.s_parse)
-            start = self.carry - carry_len
-            length = carry_len + lens[k]
-            self.s_parse.wait_event(h2d_done[b])
-            self.s_parse.wait_event(d2h_done[b])  # this buffer's previous copy-back
-            out = self._out(b)
-            self.parser.set_option(_abi.OPT_PARTIAL_INPUT, 0 if last else 1)
-            self.parser.parse_into(self.bufs[b][start:start + length], out, stream=self.s_parse)
-            parse_done[b].record(self.s_parse)
-            if not last:
-                lens[k + 1] = h2d(k + 1)  # overlaps with this partition's parse
-            prev = (b, start, length, out)
-        pb, pstart, plen, pout = prev
-        parse_done[pb].synchronize()
-        res = self._checked(pout, pb, pstart, plen, partial=False)
-        results.append(self._copy_back(self.outs[pb], res, plen, d2h_done[pb]))
-        torch.cuda.synchronize()
-        self.parser.set_option(_abi.OPT_PARTIAL_INPUT, 0)
-        return results
+                self.s_parse.wait_event(d2h_done[b])  # this buffer's previous copy-back
+                out = self._out(b)
+                self.parser.set_option(_abi.OPT_PARTIAL_INPUT, 0 if last else 1)
+                self.parser.set_option(_abi.OPT_SKIP_RECORDS, skip if k == 0 else 0)
+                self.parser.parse_into(self.bufs[b][start:start + length], out, stream=self.s_parse)
+                parse_done[b].record(self.s_parse)
+                if not last:
+                    lens[k + 1] = h2d(k + 1)  # overlaps with this partition's parse
+                prev = (b, start, length, out)
+            pb, pstart, plen, pout = prev
+            parse_done[pb].synchronize()
+            res = self._checked(pout, pb, pstart, plen, partial=False)
+            results.append(self._copy_back(self.outs[pb], res, plen, d2h_done[pb]))
+            torch.cuda.synchronize()
+            return results
+        finally:
+            self.parser.set_option(_abi.OPT_PARTIAL_INPUT, 0)
+            self.parser.set_option(_abi.OPT_SKIP_RECORDS, skip)
 
     def _checked(self, out: Output, b: int, start: int, length: int, partial: bool):
         res = out.result()

@@ -14,8 +14,9 @@ def oracle_format(name: str):
     return O.csv6() if name == "csv" else O.log8()
 
 
-def oracle_parse(dialect: str, schema, raw: bytes):
-    return O.parse(oracle_format(dialect), [OTYPE[t] if isinstance(t, str) else t for t in schema], raw)
+def oracle_parse(dialect: str, schema, raw: bytes, skip_records: int = 0):
+    return O.parse(oracle_format(dialect), [OTYPE[t] if isinstance(t, str) else t for t in schema], raw,
+                   skip_records=skip_records)
 
 
 def assert_same(got_host: dict, res, ref, rows_cap: int | None = None, what=""):
