@@ -70,6 +70,20 @@ def test_create_and_info(abi):
     p.close()
 
 
+def test_skip_records_option_bounds(abi):
+    from paper_1905_13415_gb300 import ParparawError, formats
+
+    p = _create(abi, formats.rfc4180_csv(), ["int32"])
+    for ok in (0, 1, 2**32 - 1):
+        p.set_option(abi.OPT_SKIP_RECORDS, ok)
+        assert p.skip_records == ok
+    for bad in (-1, 2**32):
+        with pytest.raises(ParparawError):
+            p.set_option(abi.OPT_SKIP_RECORDS, bad)
+    assert p.skip_records == 2**32 - 1
+    p.close()
+
+
 def test_create_rejects_bad_tables(abi):
     from paper_1905_13415_gb300 import ParparawError, formats
 
