@@ -313,8 +313,8 @@ pp_status run_launch(Launch& L, const ShapeInfo& shape, int nspec, int64_t grid_
 
 #ifdef PP_PHASE_TIMING
   if (g_phase_cycles == nullptr) {
-    cudaMalloc(reinterpret_cast<void**>(&g_phase_cycles), 16 * sizeof(unsigned long long));
-    cudaMemset(g_phase_cycles, 0, 16 * sizeof(unsigned long long));
+    cudaMalloc(reinterpret_cast<void**>(&g_phase_cycles), 32 * sizeof(unsigned long long));
+    cudaMemset(g_phase_cycles, 0, 32 * sizeof(unsigned long long));
   }
   L.phase_cycles = g_phase_cycles;
 #endif
@@ -353,12 +353,12 @@ using namespace pp;
 
 #ifdef PP_PHASE_TIMING
 // Profiling builds only (not part of include/parparaw.h): copies the
-// accumulated per-phase cycle totals of the tile kernel to out[0..15].
+// accumulated per-phase cycle totals of the tile kernel to out[0..31].
 extern "C" int parparaw_debug_phase_cycles(unsigned long long* out, int reset) {
   if (g_phase_cycles == nullptr) return -1;
   cudaDeviceSynchronize();
-  cudaMemcpy(out, g_phase_cycles, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
-  if (reset) cudaMemset(g_phase_cycles, 0, 16 * sizeof(unsigned long long));
+  cudaMemcpy(out, g_phase_cycles, 32 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (reset) cudaMemset(g_phase_cycles, 0, 32 * sizeof(unsigned long long));
   return 0;
 }
 extern "C" int parparaw_debug_last_launch(int* grid, int* per_sm) {

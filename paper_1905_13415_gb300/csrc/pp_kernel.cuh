@@ -46,7 +46,10 @@
 #include "pp_types.h"
 
 // Opt-in instrumentation (profiling builds only, -DPP_PHASE_TIMING): thread 0
-// accumulates the cycles between block-wide synchronisation points per phase.
+// accumulates the cycles between block-wide synchronisation points per phase
+// (counters 0-15); every warp times its own share of a step between two
+// marks, and each tile adds the slowest warp's time (16 + s) and the sum
+// over warps (24 + s) of span s.
 #ifdef PP_PHASE_TIMING
 #define PP_PHASE(k)                        \
   do {                                     \
@@ -56,8 +59,28 @@
       ph_last = _now;                      \
     }                                      \
   } while (0)
+#define PP_WMARK() \
+  do {             \
+    __syncwarp();  \
+    w_t0 = clock64(); \
+  } while (0)
+#define PP_WSPAN(s)                                                              \
+  do {                                                                           \
+    __syncwarp();                                                                \
+    if (lane == 0) {                                                             \
+      const unsigned long long _d = static_cast<unsigned long long>(clock64() - w_t0); \
+      atomicMax(&H->w_max[s], _d);                                               \
+      atomicAdd(&H->w_sum[s], _d);                                               \
+    }                                                                            \
+  } while (0)
 #else
 #define PP_PHASE(k) \
+  do {              \
+  } while (0)
+#define PP_WMARK() \
+  do {             \
+  } while (0)
+#define PP_WSPAN(s) \
   do {              \
   } while (0)
 #endif
@@ -85,6 +108,7 @@ struct LongField {
   uint32_t contiguous;
 };
 constexpr uint32_t kLongQ = 64;  // long fields queued per round (more are copied where found)
+constexpr uint32_t kPiece = 512;  // queued long fields are copied in pieces of this many tile bytes
 
 struct SmemHead {
   uint64_t mbar;
@@ -112,9 +136,12 @@ struct SmemHead {
   uint32_t round_tot[PP_MAX_STRING_COLUMNS];   // string bytes of the round per slot
   uint32_t round_base[PP_MAX_STRING_COLUMNS];  // string bytes of the earlier rounds
   uint32_t nlong;
+  uint32_t w2_g;         // threads per record of the round's step (2)
+  uint32_t piece_next;   // the next long-field piece to copy
   LongField longs[kLongQ];
 #ifdef PP_PHASE_TIMING
-  long long ph_cycles[16];  // profiling builds only
+  long long ph_cycles[32];  // profiling builds only
+  unsigned long long w_max[8], w_sum[8];
 #endif
   Job jd;                  // the current job and its columns, staged from the
   Col cd[PP_MAX_COLUMNS];  // launch parameters / global memory once per job
@@ -473,9 +500,12 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
   __syncthreads();
   uint32_t phase = 0;
 #ifdef PP_PHASE_TIMING
-  if (tid == 0)
-    for (int k = 0; k < 16; ++k) H->ph_cycles[k] = 0;
+  if (tid == 0) {
+    for (int k = 0; k < 32; ++k) H->ph_cycles[k] = 0;
+    for (int k = 0; k < 8; ++k) H->w_max[k] = H->w_sum[k] = 0;
+  }
   long long ph_last = clock64();
+  long long w_t0 = 0;
 #endif
 
   for (;;) {
@@ -576,6 +606,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     }
     __syncthreads();
     PP_PHASE(1);
+    PP_WMARK();
 
     // valid bytes of this thread's chunk, chunk-relative [lo, hi)
     const int64_t cv0 = static_cast<int64_t>(v0) + static_cast<int64_t>(tid) * B;
@@ -638,6 +669,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     }
 
     // ------------------------------------------- a3: o-scan + chain 1
+    PP_WSPAN(0);
     uint64_t tile_vec;
     const uint64_t vex = block_exclusive_scan<NT>(
         vec, [](uint64_t a, uint64_t b) { return vcompose(a, b); }, kIdentityVec, H->wsum64,
@@ -655,6 +687,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     const uint32_t s_start = vget(vex, tile_s0);
 
     // ------------------------------------------- a4: re-simulation, tags
+    PP_WMARK();
     uint64_t dm[MW], fm[MW], rm[MW];
 #pragma unroll
     for (int w = 0; w < MW; ++w) {
@@ -734,6 +767,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         atomicMax(&H->tile_last_rd, static_cast<unsigned long long>(cv0 + last_rd + 1 - static_cast<int64_t>(J.head)));
       if (lo < hi && cv0 + hi == static_cast<int64_t>(VL) && test_bit(rm, hi - 1)) H->eof_rd = 1u;
     }
+    PP_WSPAN(1);
     uint64_t sc_tile;
     const uint64_t sc_ex = block_exclusive_scan<NT>(
         static_cast<uint64_t>(rc_pack(nrec, ncol, nrec > 0)) | (static_cast<uint64_t>(ndat | (ndl << 16)) << 32),
@@ -759,13 +793,9 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     __syncthreads();
     PP_PHASE(5);
     // Skipping records (Sec. 4.3): record i of the input (from 0) leaves row
-    // i - S, and nothing at all for i < S.  The tile's first record is
-    // record tile_rec0, row row0 (mod 2^64); its first skip_tile records
-    // are skipped.
-    const uint64_t tile_rec0 = H->prefix_rc & kRecMask;
-    const uint64_t row0 = tile_rec0 - TB.skip_records;
-    const uint32_t skip_tile =
-        TB.skip_records > tile_rec0 ? static_cast<uint32_t>(TB.skip_records - tile_rec0) : 0u;
+    // i - S, and nothing at all for i < S.  The tile's first record is row
+    // row0 (mod 2^64).
+    const uint64_t row0 = (H->prefix_rc & kRecMask) - TB.skip_records;
     const uint32_t tile_col0 = static_cast<uint32_t>((H->prefix_rc >> 40) & 0x1FFFFF);
     const uint32_t row_start = rc_ex & 0xFFFFu;  // relative to the tile's first record
     const uint32_t col_start = (rc_ex >> 31) ? ((rc_ex >> 16) & kColSat)
@@ -814,6 +844,17 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       return e;
     };
 
+    // First non-data position in [p, e), else e.
+    auto first_gap = [&](int p, int e) -> int {
+      while (p < e) {
+        const int u = p / B, i = p - u * B, wi = i >> 6;
+        const uint64_t w = ~s_dm[u * MW + wi] & bits_below(B - 64 * wi) & ~bits_below(i & 63);
+        if (w) return min(u * B + 64 * wi + __ffsll(static_cast<long long>(w)) - 1, e);
+        p = 64 * wi + 64 >= B ? (u + 1) * B : u * B + 64 * wi + 64;
+      }
+      return e;
+    };
+
     // Field list of one round: entry i describes field f0 + i of the tile,
     // [15:0) its end position (a delimiter, or PE for the open field),
     // [15] it ends a record, [23:16] its column (saturated), [24] open field.
@@ -827,12 +868,20 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       uint32_t rr0;
     };
     const RoundStart first_round{P0 - 1, 0u};
-    // The round's first entry of a kept record (after build_round's
-    // barrier): 0 unless the round starts among the skipped records.
+    // Skipped records of a round (of nrec records from the tile's record
+    // rr0), and the round's first entry of a kept record (after
+    // build_round's barrier): 0 unless the round starts among the skipped
+    // records.  The per-entry and per-record loops start there, so they
+    // carry no test of their own.
+    auto round_skip = [&](uint32_t rr0, uint32_t nrec) -> uint32_t {
+      const uint64_t rec = (H->prefix_rc & kRecMask) + rr0;
+      const uint64_t S = TB.skip_records;
+      return rec >= S ? 0u : (S - rec < nrec ? static_cast<uint32_t>(S - rec) : nrec);
+    };
     auto first_kept = [&](uint32_t rr0, uint32_t nwin) -> uint32_t {
-      if (rr0 >= skip_tile) return 0u;
-      const uint32_t k = skip_tile - rr0;  // skipped records of the round
-      return k <= H->rr_last - rr0 ? s_rec[k] : nwin;
+      const uint32_t nrec = H->rr_last - rr0 + 1;
+      const uint32_t k = round_skip(rr0, nrec);
+      return k == 0 ? 0u : (k < nrec ? s_rec[k] : nwin);
     };
     auto build_round = [&](uint32_t f0, uint32_t f1, RoundStart r0) {
       const uint32_t rr0 = r0.rr0;
@@ -876,15 +925,15 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     // sums in s_cnt and the round totals in round_tot.
     auto count_round = [&](uint32_t nwin, RoundStart r0) {
       const uint32_t per = (nwin + NT - 1) / NT;
-      const uint32_t b0 = min(tid * per, nwin), b1 = min(b0 + per, nwin);
-      const uint32_t kept = first_kept(r0.rr0, nwin);
+      const uint32_t b1 = min(tid * per + per, nwin);
+      const uint32_t b0 = min(max(tid * per, first_kept(r0.rr0, nwin)), b1);
       for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
       uint32_t dprev = data_before(b0 == 0 ? r0.prev_pos + 1 : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu));
       for (uint32_t g = b0; g < b1; ++g) {
         const uint32_t fe = s_fe[g];
         const uint32_t de = data_before(static_cast<int>(fe & 0x7FFFu));
         const uint32_t c = (fe >> 16) & 0xFFu;
-        if (g >= kept && c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(de - dprev);
+        if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(de - dprev);
         dprev = de;
       }
       // block scan of the per-slot counts, two 16-bit slots per word
@@ -1022,16 +1071,33 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       const uint32_t rr0 = rs.rr0;
       const uint32_t nrec_win = H->rr_last - rr0 + 1;
       const int prev_pos = rs.prev_pos;
-      const uint32_t kept = first_kept(rr0, nwin);
 
       // (1) equal shares of consecutive entries: per-slot running byte
       // positions -> s_fo (field end minus data bytes before it, mod 2^16);
       // string field bytes to their columns (a lane copies a short field,
       // the warp the long ones together; nothing past a column's capacity);
       // records with a wrong field count (rare)
+      PP_WMARK();
+      if (tid == 0) {
+        // step (2) gives G threads to a record, each taking every G-th field:
+        // the G, from min(C, NT / records) up, that leaves the busiest
+        // thread the fewest fields
+        uint32_t g = max(1u, min(C, static_cast<uint32_t>(NT) / nrec_win));
+        uint32_t best = ((nrec_win * g + NT - 1) / NT) * ((C + g - 1) / g);
+        for (uint32_t g2 = g + 1, ge = min(C, g + 4); g2 <= ge; ++g2) {
+          const uint32_t cost = ((nrec_win * g2 + NT - 1) / NT) * ((C + g2 - 1) / g2);
+          if (cost < best) {
+            best = cost;
+            g = g2;
+          }
+        }
+        H->w2_g = g;
+        H->piece_next = 0;
+      }
       {
         const uint32_t per = (nwin + NT - 1) / NT;
-        const uint32_t b0 = min(tid * per, nwin), b1 = min(b0 + per, nwin);
+        const uint32_t b1 = min(tid * per + per, nwin);
+        const uint32_t b0 = min(max(tid * per, first_kept(rr0, nwin)), b1);
         for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = static_cast<uint16_t>(s_cnt[k * NT + tid] + H->round_base[k]);
         int eprev = b0 == 0 ? prev_pos : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu);
         uint32_t dprev = data_before(eprev + 1);
@@ -1047,7 +1113,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           const uint32_t c = (fe >> 16) & 0xFFu;
           if (NS > 0) {
             const uint32_t de = data_before(e);
-            if (g >= kept && c < C && TB.str_slot[c] != 0xFF) {
+            if (c < C && TB.str_slot[c] != 0xFF) {
               const uint32_t slot = TB.str_slot[c];
               const uint16_t run = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (de - dprev));
               s_cnt[slot * NT + tid] = run;
@@ -1081,7 +1147,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
             dprev = de;
           }
           eprev = e;
-          if (!INFER && g >= kept && (fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
+          if (!INFER && (fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
             // the record ends with the wrong number of fields: reject it and
             // give the missing columns their defaults
             uint32_t klo = 0, khi = nrec_win - 1;
@@ -1131,39 +1197,69 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           }
         }
       }
+      PP_WSPAN(2);
       __syncthreads();
       PP_PHASE(10);
-      // the queued long fields, a warp each, spread over all warps
-      for (uint32_t i = warp, nl = min(H->nlong, kLongQ); i < nl; i += Shape::NW) {
-        const LongField lf = H->longs[i];
-        if (lf.contiguous) {
-          warp_copy_out(lf.dst, s_tile + lf.fd, static_cast<int>(lf.nb), lane);
-        } else {  // data bytes with gaps: each lane places the bytes it holds by their rank
-          const uint32_t d0 = data_before(lf.fd);
-          for (int u = lf.fd / B; u * B < lf.e; ++u) {
-            for (int x = u * B + lane; x < (u + 1) * B; x += 32) {
-              if (x < lf.fd || x >= lf.e) continue;
-              const int ix = x - u * B;
-              if ((s_dm[u * MW + (ix >> 6)] >> (ix & 63)) & 1ull) {
-                const uint32_t rank = data_before(x) - d0;
-                if (rank < lf.nb) lf.dst[rank] = s_tile[x];
-              }
+      PP_WMARK();
+      // the queued long fields in pieces of kPiece tile bytes, spread over
+      // all warps (a whole field per warp leaves one warp copying a long
+      // text while the block waits for it)
+      {
+        const uint32_t nl = min(H->nlong, kLongQ);
+        auto pieces = [&](uint32_t i) -> uint32_t {
+          if (i >= nl) return 0u;
+          const LongField& lf = H->longs[i];
+          const uint32_t span = lf.contiguous ? lf.nb : static_cast<uint32_t>(lf.e - lf.fd);
+          return (span + kPiece - 1) / kPiece;
+        };
+        const auto add = [](uint32_t a, uint32_t b) { return a + b; };
+        static_assert(kLongQ == 64, "two queue entries per lane");
+        // inclusive piece counts over the queue: entry `lane` in s_lo, entry
+        // 32 + lane in s_hi
+        const uint32_t s_lo = warp_inclusive_scan(pieces(lane), add, lane);
+        const uint32_t s_hi = warp_inclusive_scan(pieces(lane + 32), add, lane) + __shfl_sync(0xffffffffu, s_lo, 31);
+        const uint32_t total = __shfl_sync(0xffffffffu, s_hi, 31);
+        for (;;) {  // pieces taken in turn by whichever warp is free
+          uint32_t p = 0;
+          if (lane == 0) p = atomicAdd(&H->piece_next, 1u);
+          p = __shfl_sync(0xffffffffu, p, 0);
+          if (p >= total) break;
+          // the entry holding piece p follows every entry whose pieces end at or before p
+          const uint32_t i = __popc(__ballot_sync(0xffffffffu, s_lo <= p)) + __popc(__ballot_sync(0xffffffffu, s_hi <= p));
+          const uint32_t before = __shfl_sync(0xffffffffu, i <= 32 ? s_lo : s_hi, (i + 31) & 31);
+          const uint32_t k = p - (i == 0 ? 0u : before);  // piece k of entry i
+          const LongField lf = H->longs[i];
+          const int x0 = static_cast<int>(lf.fd + k * kPiece);
+          if (lf.contiguous) {
+            warp_copy_out(lf.dst + k * kPiece, s_tile + x0, static_cast<int>(min(kPiece, lf.nb - k * kPiece)), lane);
+          } else {  // data bytes with gaps (a doubled quote, say): its runs of data bytes one by one
+            const uint32_t d0 = data_before(lf.fd);
+            const int x1 = min(x0 + static_cast<int>(kPiece), static_cast<int>(lf.e));
+            for (int a = first_data(x0, x1); a < x1;) {
+              const int z = first_gap(a, x1);
+              const uint32_t rank = data_before(a) - d0;
+              if (rank >= lf.nb) break;
+              warp_copy_out(lf.dst + rank, s_tile + a, min(z - a, static_cast<int>(lf.nb - rank)), lane);
+              a = first_data(z, x1);
             }
           }
         }
       }
 
+      PP_WSPAN(3);
+      PP_WMARK();
       // (2) string offsets and numeric conversions, record by record: G
-      // threads per record take every G-th field (G = 1 when records are
-      // at least as many as threads: lanes of a warp then take consecutive
-      // records column by column)
-      const uint32_t G = max(1u, min(C, static_cast<uint32_t>(NT) / nrec_win));
+      // threads per record take every G-th field (G chosen in step (1)).
+      // Work item j is share j / nk of record j % nk, so the lanes of a warp
+      // take consecutive records and store each column side by side.
+      const uint32_t G = H->w2_g;  // written before the barrier after step (1)
+      const uint32_t ks = round_skip(rr0, nrec_win);  // skipped records lead the round
+      const uint32_t nk = nrec_win - ks;
       if constexpr (INFER) {
         // (2') inference: the fields of each record that ends here, and the
         // narrowest type of every non-empty field that starts here
-        for (uint32_t j = tid; j < nrec_win * G; j += NT) {
-          const uint32_t k = j / G, sub = j - k * G;
-          if (rr0 + k < skip_tile) continue;
+        for (uint32_t j = tid; j < nk * G; j += NT) {
+          const uint32_t sub = j / nk, k = ks + (j - sub * nk);
           const uint32_t gb = s_rec[k], ge = k + 1 < nrec_win ? s_rec[k + 1] : nwin;
           if (sub == 0 && ge > gb) {
             const uint32_t fl = s_fe[ge - 1];
@@ -1225,11 +1321,10 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           }
         }
       } else
-      for (uint32_t j = tid; j < nrec_win * G; j += NT) {
-        const uint32_t k = j / G, sub = j - k * G;
-        if (rr0 + k < skip_tile) continue;
+      for (uint32_t j = tid; j < nk * G; j += NT) {
+        const uint32_t sub = j / nk, k = ks + (j - sub * nk);
         const uint64_t row = row0 + rr0 + k;
-        if (row >= rows_cap) break;
+        if (row >= rows_cap) continue;
         const uint32_t gb = s_rec[k], ge = k + 1 < nrec_win ? s_rec[k + 1] : nwin;
         for (uint32_t g = gb + sub; g < ge; g += G) {
           const uint32_t fe = s_fe[g];
@@ -1249,6 +1344,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         }
       }
 
+      PP_WSPAN(4);
       PP_PHASE(11);
       __syncthreads();
       PP_PHASE(12);
@@ -1260,18 +1356,27 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       if (tid == PP_MAX_COLUMNS + 1 && s_inf[tid]) atomicMax(&J.misc->inf_max_fields, s_inf[tid]);
     }
     if (last_tile && tid == 0) {
-      const uint32_t recs = rec_tile + (trailing ? 1u : 0u);  // of the tile; rows: read by the finalize kernel only
-      J.misc->rows = recs >= skip_tile ? static_cast<int64_t>(row0 + recs) : 0;
+      const uint64_t recs = (H->prefix_rc & kRecMask) + rec_tile + (trailing ? 1u : 0u);  // of the input
+      J.misc->rows = static_cast<int64_t>(recs > TB.skip_records ? recs - TB.skip_records : 0u);  // read by the finalize kernel only
       J.misc->final_state = static_cast<int32_t>(tile_send);
       for (uint32_t k = 0; k < NS; ++k) J.misc->bytes_total[k] = H->col_base[k] + H->tile_tot[k];
       J.misc->done = 1u;
     }
 
     PP_PHASE(9);  // the last barrier of the round loop ends the tile
+#ifdef PP_PHASE_TIMING
+    if (tid == 0) {  // every warp's spans of this tile ended before that barrier
+      for (int k = 0; k < 8; ++k) {
+        H->ph_cycles[16 + k] += static_cast<long long>(H->w_max[k]);
+        H->ph_cycles[24 + k] += static_cast<long long>(H->w_sum[k]);
+        H->w_max[k] = H->w_sum[k] = 0;
+      }
+    }
+#endif
   }
 #ifdef PP_PHASE_TIMING
   if (tid == 0 && L.phase_cycles != nullptr)
-    for (int k = 0; k < 16; ++k) atomicAdd(&L.phase_cycles[k], static_cast<unsigned long long>(H->ph_cycles[k]));
+    for (int k = 0; k < 32; ++k) atomicAdd(&L.phase_cycles[k], static_cast<unsigned long long>(H->ph_cycles[k]));
 #endif
 }
 
