@@ -205,6 +205,7 @@ __device__ __forceinline__ int window_take(uint32_t valid, uint32_t inc, bool* d
 // at most one window of predecessors per round trip, which bounds how fast the
 // inclusive prefixes propagate through the tiles.)
 constexpr int kLbRounds = 4;
+constexpr int kLbRoundsSums = 4;  // the same for the per-slot byte counts
 
 // Called by one full warp.  Publishes the tile's aggregate, walks back over
 // predecessors until an inclusive prefix is found, publishes the tile's
@@ -288,14 +289,14 @@ static __device__ int64_t lookback_sums(uint64_t* st, uint64_t t, uint32_t ns, c
     bool mydone = !active;  // this lane's chain found its inclusive prefix
     int64_t base = static_cast<int64_t>(t) - 1;
     while (__any_sync(0xffffffffu, !mydone)) {
-      uint64_t w[kLbRounds];
+      uint64_t w[kLbRoundsSums];
 #pragma unroll
-      for (int j = 0; j < kLbRounds; ++j) {
+      for (int j = 0; j < kLbRoundsSums; ++j) {
         const int64_t mine = base - (per * j + i);
         w[j] = (active && mine >= 0) ? ld_relaxed_u64(&st[mine * ns + k]) : kFlagInc;
       }
 #pragma unroll
-      for (int j = 0; j < kLbRounds; ++j) {
+      for (int j = 0; j < kLbRoundsSums; ++j) {
         const int64_t mine = base - (per * j + i);
         int limit = -1;  // include lanes of chain k up to this lane index
         bool done_now = false;
@@ -334,7 +335,7 @@ static __device__ int64_t lookback_sums(uint64_t* st, uint64_t t, uint32_t ns, c
         acc += x;
         if (done_now) mydone = true;
       }
-      base -= per * kLbRounds;
+      base -= per * kLbRoundsSums;
     }
   }
   if (lane < static_cast<int>(ns))
@@ -1219,11 +1220,13 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         const uint32_t s_lo = warp_inclusive_scan(pieces(lane), add, lane);
         const uint32_t s_hi = warp_inclusive_scan(pieces(lane + 32), add, lane) + __shfl_sync(0xffffffffu, s_lo, 31);
         const uint32_t total = __shfl_sync(0xffffffffu, s_hi, 31);
-        for (;;) {  // pieces taken in turn by whichever warp is free
-          uint32_t p = 0;
-          if (lane == 0) p = atomicAdd(&H->piece_next, 1u);
-          p = __shfl_sync(0xffffffffu, p, 0);
-          if (p >= total) break;
+        // pieces taken in turn by whichever warp is free; a warp takes its
+        // next piece before it copies the one in hand
+        uint32_t p = 0;
+        if (lane == 0) p = atomicAdd(&H->piece_next, 1u);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        for (uint32_t pn = 0; p < total; p = __shfl_sync(0xffffffffu, pn, 0)) {
+          if (lane == 0) pn = atomicAdd(&H->piece_next, 1u);
           // the entry holding piece p follows every entry whose pieces end at or before p
           const uint32_t i = __popc(__ballot_sync(0xffffffffu, s_lo <= p)) + __popc(__ballot_sync(0xffffffffu, s_hi <= p));
           const uint32_t before = __shfl_sync(0xffffffffu, i <= 32 ? s_lo : s_hi, (i + 31) & 31);
