@@ -201,11 +201,12 @@ __device__ __forceinline__ int window_take(uint32_t valid, uint32_t inc, bool* d
 }
 
 // Look-back windows: each lane loads kLbRounds status words at once, so one
-// round trip to L2 covers 32 * kLbRounds predecessors.  (A chain can resolve
-// at most one window of predecessors per round trip, which bounds how fast the
-// inclusive prefixes propagate through the tiles.)
-constexpr int kLbRounds = 4;
-constexpr int kLbRoundsSums = 4;  // the same for the per-slot byte counts
+// round trip to L2 covers 32 * kLbRounds predecessors (32 / slots * kLbRounds
+// per byte-count chain).  One word per lane measured fastest: an inclusive
+// prefix is nearly always within reach, and wider windows cost registers in
+// the whole kernel.
+constexpr int kLbRounds = 1;
+constexpr int kLbRoundsSums = 1;  // the same for the per-slot byte counts
 
 // Called by one full warp.  Publishes the tile's aggregate, walks back over
 // predecessors until an inclusive prefix is found, publishes the tile's
