@@ -111,6 +111,9 @@ def lib():
         L.ppo_infer_skip.argtypes = [ctypes.POINTER(_Format), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
                                      ctypes.POINTER(_Inference)]
         L.ppo_infer_skip.restype = ctypes.c_int
+        L.ppo_skip_rows.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
+                                    ctypes.c_uint8, ctypes.c_void_p]
+        L.ppo_skip_rows.restype = ctypes.c_size_t
         _lib = L
     return _lib
 
@@ -351,3 +354,13 @@ def infer(fmt: Format, data, skip_records: int = 0) -> Inference:
     lib().ppo_infer_skip(ctypes.byref(fmt._c), buf.ctypes.data, len(buf), ctypes.c_uint64(skip_records),
                          ctypes.byref(r))
     return Inference(r.status, r.min_fields, r.max_fields, r.records, r.first_invalid_offset, list(r.type))
+
+
+def skip_rows(data, rows, terminator: int = 0x0A) -> bytes:
+    """Sec. 4.3, skipping rows (see ppo_skip_rows): the input without the
+    physical lines listed in ``rows`` (sorted, distinct)."""
+    buf = np.frombuffer(bytes(data), dtype=np.uint8)
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.uint64))
+    out = np.empty(max(len(buf), 1), np.uint8)
+    n = lib().ppo_skip_rows(buf.ctypes.data, len(buf), r.ctypes.data, len(r), terminator, out.ctypes.data)
+    return out[:n].tobytes()

@@ -547,3 +547,18 @@ int ppo_infer_skip(const ppo_format* f, const uint8_t* in, size_t len, uint64_t 
   out->first_invalid_offset = first_invalid;
   return 0;
 }
+
+/* Sec. 4.3, skipping rows: the pruning pass, one byte at a time.  `next`
+ * walks the sorted list of skipped rows alongside the current row. */
+size_t ppo_skip_rows(const uint8_t* in, size_t len, const uint64_t* rows, size_t nrows,
+                     uint8_t terminator, uint8_t* out) {
+  uint64_t row = 0;
+  size_t next = 0, n = 0;
+  for (size_t i = 0; i < len; ++i) {
+    while (next < nrows && rows[next] < row) ++next;
+    const int skipped = next < nrows && rows[next] == row;
+    if (!skipped) out[n++] = in[i];
+    if (in[i] == terminator) ++row;
+  }
+  return n;
+}

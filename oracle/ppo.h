@@ -139,6 +139,14 @@ typedef struct ppo_inference {
   uint8_t type[PPO_MAX_COLUMNS];
 } ppo_inference;
 int ppo_infer(const ppo_format* f, const uint8_t* in, size_t len, ppo_inference* out);
+
+/* Sec. 4.3, skipping rows: a row is a physical line, its bytes up to and
+ * including the next `terminator` byte (the last row may lack it), whatever
+ * the quoting; rows count from 0.  Copies to out (capacity >= len) the bytes
+ * of every row not listed in rows[0..nrows) (strictly increasing) and
+ * returns how many it copied.  The parse then runs on what is left. */
+size_t ppo_skip_rows(const uint8_t* in, size_t len, const uint64_t* rows, size_t nrows,
+                     uint8_t terminator, uint8_t* out);
 int ppo_infer_skip(const ppo_format* f, const uint8_t* in, size_t len, uint64_t skip_records,
                    ppo_inference* out);  /* ppo_infer over all but the first skip_records records */
 

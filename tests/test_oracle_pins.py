@@ -425,3 +425,35 @@ def test_inference_skips_a_header_record():
     assert (k.types, k.records, k.min_fields, k.max_fields, k.status) == \
         (b.types, b.records, b.min_fields, b.max_fields, b.status)
     assert O.infer(O.csv6(), raw, skip_records=9).records == 0
+
+
+def _lines_without(raw: bytes, rows, term: bytes = b"\n") -> bytes:
+    """The definition of skipping rows written with bytes.split: a row is a
+    physical line with its terminator; the last one may lack it."""
+    parts = raw.split(term)
+    lines = [p + term for p in parts[:-1]] + ([parts[-1]] if parts[-1] else [])
+    drop = set(rows)
+    return b"".join(line for i, line in enumerate(lines) if i not in drop)
+
+
+def test_skip_rows_matches_the_line_split_definition():
+    # Sec. 4.3, skipping rows: the pruning pass against bytes.split
+    rng = random.Random(11)
+    for it in range(400):
+        term = b"\n" if it % 3 else b";"
+        raw = bytes(rng.choice(b'ab"\n,;') for _ in range(rng.randint(0, 300)))
+        nl = raw.count(term) + 1
+        rows = sorted(rng.sample(range(nl + 3), rng.randint(0, min(nl + 3, 12))))
+        assert O.skip_rows(raw, rows, term[0]) == _lines_without(raw, rows, term), (it, raw, rows)
+
+
+def test_skip_rows_is_not_skip_records():
+    # rows are physical lines: dropping a header row equals skipping the
+    # header record, but dropping a row inside a quoted field breaks the record
+    body = b'1,"x\ny"\n2,z\n'
+    raw = b"id,name\n" + body
+    a = O.parse(O.csv6(), [O.INT32, O.STRING], O.skip_rows(raw, [0]))
+    b = O.parse(O.csv6(), [O.INT32, O.STRING], raw, skip_records=1)
+    assert (a.rows, a.field(0, 1), a.field(1, 1)) == (b.rows, b.field(0, 1), b.field(1, 1)) == (2, b"x\ny", b"z")
+    c = O.parse(O.csv6(), [O.INT32, O.STRING], O.skip_rows(raw, [1]))  # leaves 'y",..' : a stray quote
+    assert c.status == O.E_INVALID_INPUT
