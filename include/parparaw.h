@@ -334,6 +334,32 @@ typedef struct pp_inference {
 pp_status parparaw_infer(const pp_parser* parser, const uint8_t* input, uint64_t len,
                          pp_inference* result, void* stream);
 
+/* Skipping rows (Sec. 4.3): the pruning pass that runs before a parse.  A
+ * row is a physical line: its bytes up to and including the next
+ * `terminator` byte (the last row may lack it), whatever the quoting; rows
+ * count from 0.  Rows differ from records (a quoted field may span lines), so
+ * rows are pruned from the raw bytes, before the DFA sees them.
+ *   input[0..len)      device memory, read only.
+ *   rows[0..nrows)     device memory: the rows to drop, strictly increasing;
+ *                      with any other list the output is unspecified (every
+ *                      access still stays in bounds).  Rows past the end are
+ *                      ignored.
+ *   output             device memory, capacity >= len, not overlapping input:
+ *                      the bytes of every other row, in order.
+ *   output_len         device memory (one uint64_t): the bytes written.
+ *   scratch            device memory of scratch_bytes >=
+ *                      parparaw_skip_rows_scratch_bytes(len), 16-byte aligned,
+ *                      owned by the caller and not used by anything else
+ *                      until the stream has passed this call.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = default stream); a parse
+ * of output[0..*output_len) follows on the same stream once the caller has
+ * read *output_len.  Returns PP_E_ARG for NULL pointers with len > 0 or a
+ * scratch that is too small or misaligned, PP_E_CUDA if a launch fails. */
+uint64_t parparaw_skip_rows_scratch_bytes(uint64_t len);
+pp_status parparaw_skip_rows(const uint8_t* input, uint64_t len, const uint64_t* rows, uint64_t nrows,
+                             uint8_t terminator, uint8_t* output, uint64_t* output_len, void* scratch,
+                             uint64_t scratch_bytes, void* stream);
+
 /* Records the two CUDA events (cudaEvent_t passed as void*) on the stream
  * immediately before and after the main parse kernel of every later parse or
  * batch made with this parser, so that a caller can time that kernel alone.

@@ -8,11 +8,12 @@ CPU fallback: without the library every parse raises.
 from . import formats  # noqa: F401
 from ._abi import TYPE_NAMES, status_string  # noqa: F401
 
-__all__ = ["formats", "Parser", "Output", "Result", "ParparawError", "parse_batch", "Batch", "status_string"]
+__all__ = ["formats", "Parser", "Output", "Result", "ParparawError", "parse_batch", "Batch", "skip_rows",
+           "status_string"]
 
 
 def __getattr__(name):
-    if name in ("Parser", "Output", "Result", "ParparawError", "parse_batch", "Batch"):
+    if name in ("Parser", "Output", "Result", "ParparawError", "parse_batch", "Batch", "skip_rows"):
         from . import parser as _p
 
         return getattr(_p, name)

@@ -23,7 +23,8 @@ OPT_TILE_CONFIG, OPT_TIMEOUT_MS, OPT_GRID_LIMIT, OPT_PARTIAL_INPUT, OPT_FIRST_IT
 EXPORTED = ["parparaw_create", "parparaw_destroy", "parparaw_set_option", "parparaw_get_info",
             "parparaw_parse", "parparaw_parse_batch", "parparaw_set_kernel_events",
             "parparaw_status_string", "parparaw_parse_noalloc", "parparaw_batch_create",
-            "parparaw_batch_launch", "parparaw_batch_destroy", "parparaw_infer"]
+            "parparaw_batch_launch", "parparaw_batch_destroy", "parparaw_infer",
+            "parparaw_skip_rows_scratch_bytes", "parparaw_skip_rows"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -131,6 +132,11 @@ def load():
     L.parparaw_set_kernel_events.restype = ctypes.c_int
     L.parparaw_infer.argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
     L.parparaw_infer.restype = ctypes.c_int
+    L.parparaw_skip_rows_scratch_bytes.argtypes = [ctypes.c_uint64]
+    L.parparaw_skip_rows_scratch_bytes.restype = ctypes.c_uint64
+    L.parparaw_skip_rows.argtypes = [vp, ctypes.c_uint64, vp, ctypes.c_uint64, ctypes.c_uint8, vp, vp, vp,
+                                     ctypes.c_uint64, vp]
+    L.parparaw_skip_rows.restype = ctypes.c_int
     L.parparaw_status_string.argtypes = [ctypes.c_int]
     L.parparaw_status_string.restype = ctypes.c_char_p
     _lib = L

@@ -312,3 +312,31 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def skip_rows(data: torch.Tensor, rows, terminator: bytes = b"\n", stream=None) -> torch.Tensor:
+    """Sec. 4.3, skipping rows (parparaw_skip_rows): ``data`` (a device uint8
+    tensor) without the physical lines listed in ``rows`` (row numbers from
+    0, strictly increasing).  Returns a new device tensor holding the bytes
+    that stay; waits for the pass to learn their count."""
+    lib = _abi.load()
+    if data.device.type != "cuda" or data.dtype != torch.uint8 or not data.is_contiguous():
+        raise ParparawError(_abi.E_ARG, "skip_rows wants a contiguous device uint8 tensor")
+    r = torch.as_tensor(list(rows) if not isinstance(rows, torch.Tensor) else rows, dtype=torch.int64)
+    if r.numel() > 1 and not bool((r[1:] > r[:-1]).all()):
+        raise ParparawError(_abi.E_ARG, "rows must be strictly increasing")
+    if r.numel() and int(r[0]) < 0:
+        raise ParparawError(_abi.E_ARG, "rows are numbered from 0")
+    r = r.to(data.device)
+    n = data.numel()
+    out = torch.empty(max(n, 1), dtype=torch.uint8, device=data.device)
+    out_len = torch.zeros(1, dtype=torch.int64, device=data.device)
+    sb = int(lib.parparaw_skip_rows_scratch_bytes(n))
+    scratch = torch.empty(sb, dtype=torch.uint8, device=data.device)
+    rc = lib.parparaw_skip_rows(data.data_ptr() if n else None, n, r.data_ptr() if r.numel() else None, r.numel(),
+                                terminator[0], out.data_ptr(), out_len.data_ptr(), scratch.data_ptr(), sb,
+                                _stream(stream))
+    if rc != _abi.OK:
+        raise ParparawError(rc, "parparaw_skip_rows")
+    torch.cuda.synchronize(data.device)
+    return out[: int(out_len.item())]

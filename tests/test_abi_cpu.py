@@ -156,3 +156,16 @@ def test_parse_rejects_bad_arguments_without_gpu(abi):
     assert rc == abi.E_ARG
     assert lib.parparaw_parse_batch(None, 1, None) == abi.E_ARG
     assert lib.parparaw_parse_batch(None, 0, None) == abi.OK
+
+
+def test_skip_rows_rejects_bad_arguments_without_gpu(abi):
+    lib = abi.load()
+    need = lib.parparaw_skip_rows_scratch_bytes(100_000)
+    assert need >= 24 * ((100_000 + 16383) // 16384)
+    fake = 4096  # never dereferenced: every call below fails its argument checks first
+    E = abi.E_ARG
+    assert lib.parparaw_skip_rows(fake, 10, None, 0, 10, fake, None, fake, need, None) == E  # no output_len
+    assert lib.parparaw_skip_rows(None, 10, None, 0, 10, fake, fake, fake, need, None) == E  # no input
+    assert lib.parparaw_skip_rows(fake, 10, None, 3, 10, fake, fake, fake, need, None) == E  # rows missing
+    assert lib.parparaw_skip_rows(fake, 100_000, None, 0, 10, fake, fake, fake, need - 1, None) == E  # scratch
+    assert lib.parparaw_skip_rows(fake, 10, None, 0, 10, fake, fake, fake + 8, need, None) == E  # misaligned
