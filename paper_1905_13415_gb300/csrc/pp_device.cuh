@@ -89,6 +89,11 @@ __device__ __forceinline__ void tma_load_1d(void* sdst, const void* gsrc, uint32
       "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// global -> L2 bulk prefetch (no destination, no completion); 16-byte
+// aligned, size % 16 == 0
+__device__ __forceinline__ void prefetch_l2_bulk(const void* gsrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
+}
 // shared -> global bulk copy (TMA, non-tensor), bulk-group completion
 __device__ __forceinline__ void tma_store_1d(void* gdst, const void* ssrc, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),

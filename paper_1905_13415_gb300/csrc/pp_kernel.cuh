@@ -585,6 +585,15 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&H->mbar, bulk);
       tma_load_1d(s_tile + (a16 - v0), vbase + a16, bulk, &H->mbar);
+      // The tile a block will take about one tile from now (tiles go out in
+      // order, one per resident block per tile time) is pulled into L2, so
+      // its load waits on L2 rather than HBM.
+      const uint64_t tn = t + gridDim.x;
+      if (tn < J.ntiles) {
+        const uint64_t pa = max(tn * T, (J.head + 15) & ~uint64_t(15));
+        const uint64_t pb = min(tn * T + T, VL & ~uint64_t(15));
+        if (pb > pa) prefetch_l2_bulk(vbase + pa, static_cast<uint32_t>(pb - pa));
+      }
     }
     {
       const uint64_t lo_v = max(v0, J.head);
