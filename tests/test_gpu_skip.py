@@ -131,3 +131,26 @@ def test_streamed_skip_applies_to_the_first_partition_only(pp):
             assert np.array_equal(vals.view(np.uint8), col.values.view(np.uint8))
         valid = np.concatenate([_bits(x.columns[c]["validity"].numpy(), x.rows) for x in parts])
         assert np.array_equal(valid, _bits(col.validity, ref.rows))
+
+
+def test_batch_items_keep_their_own_skip(pp):
+    # one batched launch of parsers with different skips (and a selected
+    # column) equals each plain parse against the oracle
+    items, refs = [], []
+    for k, (workload, n, skip) in enumerate([("mixed", 2000, 0), ("mixed", 1500, 3), ("log", 2500, 1),
+                                             ("review", 200, 7), ("trip", 3000, 2999), ("mixed", 10, 20)]):
+        raw, _ = synth.records(workload, 80 + k, 0, n)
+        schema = list(synth.SCHEMAS[workload])
+        if k == 1:
+            schema[1] = "skip"
+        dialect = synth.DIALECT[workload]
+        p = pp.Parser(pp.formats.by_name(dialect), schema, tile_config=2, skip_records=skip)
+        data = _dev(raw)
+        out = p.allocate(max(n, 1), [len(raw) + 1] * len(schema))
+        items.append((p, data, out))
+        refs.append(oracle_parse(dialect, schema, raw, skip))
+    pp.parse_batch(items)
+    torch.cuda.synchronize()
+    for k, ((p, data, out), ref) in enumerate(zip(items, refs)):
+        res = out.result()
+        assert_same(out.to_host(min(res.rows, out.rows_cap)), res, ref, what=("batch item", k))
