@@ -6,7 +6,8 @@
 // blocks that are already running.  Per tile:
 //
 //   load    TMA bulk copy of the tile into shared memory (ragged ends by
-//           plain loads); 16-byte vector reads per thread.
+//           plain loads); 16-byte vector reads per thread.  The tile a block
+//           will take one tile-time later is bulk-prefetched into L2.
 //   a1, a2  symbol matching (SWAR zero-byte tests against the symbols,
 //           Sec. 4.5) and multi-state simulation of the chunk: one DFA
 //           instance per state, packed as a state-transition vector
@@ -27,11 +28,12 @@
 //           holds are processed in rounds.
 //   a6      stable partition (Sec. 3.3): over equal shares of the entries,
 //           each string field's running offset and its data bytes straight
-//           from the tile to the column (long fields queued and copied by
-//           whole warps, 16-byte stores); Arrow int64 offsets per record.
-//   a7      numeric fields are converted one record per thread (or several
-//           threads per record when the tile holds few records), column by
-//           column (Sec. 3.3).
+//           from the tile to the column (long fields queued, then copied in
+//           512-byte pieces taken by free warps, 16-byte stores); Arrow
+//           int64 offsets per record.
+//   a7      numeric fields are converted by G threads per record (G chosen
+//           per round to balance the threads), lanes of a warp on
+//           consecutive records, column by column (Sec. 3.3).
 //   a8      invalid transitions, field-count mismatches and conversion
 //           failures are recorded; the finalize kernel turns them into
 //           validity bitmaps and the result.
@@ -460,8 +462,8 @@ __device__ __forceinline__ void warp_copy_out(uint8_t* dst, const uint8_t* src, 
   if (lane < (n & 15)) dst[16 * nv + lane] = src[16 * nv + lane];
 }
 
-// String fields with more data bytes in a tile than this are copied by a
-// whole warp.
+// String fields with more data bytes in a tile than this are queued and
+// copied by the block's warps together.
 constexpr uint32_t kLongField = 40;
 
 __device__ __forceinline__ void store_value(const Col& col, uint32_t type, uint64_t r, uint64_t v) {
@@ -1137,7 +1139,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
                   gdst = static_cast<uint8_t*>(cols[c].values) + off;
                   fd = first_data(eprev + 1, e);
                   contiguous = data_before(fd + static_cast<int>(nb)) == dprev + nb;
-                  if (nb > kLongField) {  // queued for any warp, else copied by this warp below
+                  if (nb > kLongField) {  // queued for the block, else (queue full) copied by this warp below
                     const uint32_t q = atomicAdd(&H->nlong, 1u);
                     if (q < kLongQ) {
                       H->longs[q] = LongField{gdst, static_cast<uint16_t>(fd), static_cast<uint16_t>(e), nb,
