@@ -239,9 +239,50 @@ def run_other_configs(args, dev, log):
             out["trip_infer"] = {"input_bytes": n, "ms_median": round(imed, 4),
                                  "GB/s": round(n / (imed * 1e-3) / 1e9, 3), "runs": reps,
                                  "min_fields": inf.min_fields, "max_fields": inf.max_fields}
+            out["trip_skip_rows"] = time_skip_rows(data, rows, reps, stream)
         del o, data, host
         torch.cuda.empty_cache()
     return out
+
+
+def time_skip_rows(data, rows, reps, stream):
+    """Skipping rows (Sec. 4.3) over a resident input: every 100th line
+    dropped by the pruning pre-pass (parparaw_skip_rows), buffers allocated
+    once, device time of the pass alone."""
+    import numpy as np
+    import torch
+
+    from paper_1905_13415_gb300 import _abi
+
+    lib = _abi.load()
+    n = data.numel()
+    drop = torch.arange(0, rows, 100, dtype=torch.int64, device=data.device)
+    outb = torch.empty(n, dtype=torch.uint8, device=data.device)
+    out_len = torch.zeros(1, dtype=torch.int64, device=data.device)
+    sb = int(lib.parparaw_skip_rows_scratch_bytes(n))
+    scratch = torch.empty(sb, dtype=torch.uint8, device=data.device)
+
+    def once():
+        rc = lib.parparaw_skip_rows(data.data_ptr(), n, drop.data_ptr(), drop.numel(), 0x0A, outb.data_ptr(),
+                                    out_len.data_ptr(), scratch.data_ptr(), sb, stream.cuda_stream)
+        assert rc == _abi.OK, rc
+
+    for _ in range(3):
+        once()
+    t = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        once()
+        e1.record(stream)
+        e1.synchronize()
+        t.append(e0.elapsed_time(e1))
+    kept = int(out_len.item())
+    assert 0 < kept < n
+    med = float(np.median(t))
+    return {"input_bytes": n, "rows_dropped": int(drop.numel()), "bytes_kept": kept, "ms_median": round(med, 4),
+            "GB/s": round(n / (med * 1e-3) / 1e9, 3), "runs": reps,
+            "note": "every 100th line pruned before the parse; 3 reads of the input, 1 write of what stays"}
 
 
 def run_batched(args, dev, log):

@@ -87,3 +87,17 @@ def test_parse_after_skipping_rows(pp):
 def test_unsorted_rows_are_refused(pp):
     with pytest.raises(pp.ParparawError):
         pp.skip_rows(_dev(b"a\nb\n"), [1, 0])
+
+
+@pytest.mark.parametrize("offset", [1, 3, 7, 13, 15])
+def test_unaligned_input(pp, offset):
+    # the input starting anywhere in a 16-byte block, ends ragged
+    g = np.random.default_rng(offset)
+    b = g.integers(0x20, 0x7F, 50_000 + offset, dtype=np.uint8)
+    b[g.random(b.size) < 0.05] = 0x0A
+    raw = b.tobytes()
+    dev = torch.frombuffer(bytearray(b"\0" * offset + raw), dtype=torch.uint8).to("cuda")[offset:]
+    nl = raw.count(b"\n") + 1
+    for rows in ([], [0], list(range(0, nl, 7)), [nl - 1], list(range(nl))):
+        got = pp.skip_rows(dev, rows).cpu().numpy().tobytes()
+        assert got == O.skip_rows(raw, rows), (offset, len(rows))
