@@ -354,23 +354,6 @@ __device__ __forceinline__ void set_range(uint64_t (&m)[MW], int lo, int hi) {
   for (int w = 0; w < MW; ++w) m[w] |= bit_range(lo - 64 * w, hi - 64 * w);
 }
 template <int MW>
-__device__ __forceinline__ int popc_range(const uint64_t (&m)[MW], int lo, int hi) {
-  int n = 0;
-#pragma unroll
-  for (int w = 0; w < MW; ++w) n += __popcll(m[w] & bit_range(lo - 64 * w, hi - 64 * w));
-  return n;
-}
-// first position >= x (and < end) whose bit equals `one`, else end
-template <int MW>
-__device__ __forceinline__ int next_bit(const uint64_t (&m)[MW], int x, int end, bool one) {
-#pragma unroll
-  for (int w = 0; w < MW; ++w) {
-    const uint64_t v = (one ? m[w] : ~m[w]) & ~bits_below(x - 64 * w);
-    if (v && 64 * w + 63 >= x) return min(64 * w + __ffsll(static_cast<long long>(v)) - 1, end);
-  }
-  return end;
-}
-template <int MW>
 __device__ __forceinline__ bool test_bit(const uint64_t (&m)[MW], int p) {
   bool r = false;
 #pragma unroll
