@@ -539,15 +539,19 @@ def main():
         ksteps = max(2, min(args.steps, 5))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        e2e_step_ms = []
         for _ in range(ksteps):
-            got_rows, parts = e2e_step()
+            ts = time.perf_counter()
+            got_rows, parts = e2e_step()  # returns with the stream drained
+            e2e_step_ms.append((time.perf_counter() - ts) * 1e3)
             del parts
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / ksteps
         (e2e_ms,) = max_over_ranks([e2e_ms], world, dev)
         e2e = {"value": round(whole_job_rate(world, n, e2e_ms), 3), "unit": "GB/s",
                "h2d_bytes_per_step": n, "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
-               "steps": ksteps, "api": "StreamParser.parse (partitioned, overlapped, carry-over)",
+               "steps": ksteps, "step_ms": [round(x, 2) for x in e2e_step_ms],
+               "api": "StreamParser.parse (partitioned, overlapped, carry-over)",
                "partition_bytes": args.partition_bytes}
         del sp
 
