@@ -296,7 +296,9 @@ void parparaw_batch_destroy(pp_batch* batch);
  *     the number of numeric columns) exceeds PP_NOALLOC_SCRATCH_BYTES.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: after cudaDeviceReset on a device the array moves, so this
+ *     entry point must not be called on that device again.
  *   - Every call on a device shares the one array and it keeps the previous
  *     call's contents; each call clears what must start at zero itself.
  *     Calls whose work overlaps on the GPU (other streams, other threads)

@@ -924,35 +924,8 @@ extern "C" pp_status parparaw_parse_noalloc(const pp_parser* P, const uint8_t* i
   L.first_item = P->first_item;
   L.timeout_ns = P->timeout_ns;
 
-  // init clears everything the tile kernel needs at zero (status words,
-  // bitmaps, counters), since the array keeps the previous call's contents
-  const uint32_t gx_init = static_cast<uint32_t>(std::max<uint64_t>(
-      1, std::min<uint64_t>((std::max(J.ntiles * std::max<uint32_t>(1, P->tab.num_str), J.bit_words * 16) +
-                             kBlockInit - 1) / kBlockInit, 1024)));
-  pp_init_kernel<<<dim3(gx_init, 1), kBlockInit, 0, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return map_err(e);
-  if (L.total_tiles > 0) {
-    const void* kern = shape.kernel(nspec_of(P->tab));
-    int sms = 0, per_sm = 0;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return map_err(e);
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(shape.smem_bytes))) != cudaSuccess)
-      return map_err(e);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, shape.threads, shape.smem_bytes)) !=
-        cudaSuccess)
-      return map_err(e);
-    uint64_t grid = std::min<uint64_t>(L.total_tiles, static_cast<uint64_t>(std::max(per_sm, 1)) * sms);
-    if (P->grid_limit > 0) grid = std::min<uint64_t>(grid, static_cast<uint64_t>(P->grid_limit));
-    if (P->ev_start) cudaEventRecord(P->ev_start, stream);
-    void* args[] = {&L};
-    if ((e = cudaLaunchKernel(kern, dim3(static_cast<uint32_t>(grid)), dim3(shape.threads), args, shape.smem_bytes,
-                              stream)) != cudaSuccess)
-      return map_err(e);
-    if (P->ev_stop) cudaEventRecord(P->ev_stop, stream);
-  }
-  const uint32_t gx_fin = static_cast<uint32_t>(
-      std::max<uint64_t>(1, std::min<uint64_t>((J.bit_words + kBlockFinal - 1) / kBlockFinal, 1024)));
-  pp_finalize_kernel<<<dim3(gx_fin, 1), kBlockFinal, 0, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return map_err(e);
-  return PP_OK;
+  // the same launch sequence as parparaw_parse: the init kernel clears
+  // everything the tile kernel needs at zero (status words, bitmaps,
+  // counters), since the array keeps the previous call's contents
+  return run_launch(L, shape, nspec_of(P->tab), P->grid_limit, P, stream, 1, J.ntiles, J.bit_words);
 }

@@ -591,16 +591,28 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         if (in_head || in_tail) s_tile[x - v0] = vbase[x];
       }
     }
+    bool load_expired = false;
     if (bulk > 0) {
       while (!mbar_try_wait(&H->mbar, phase)) {
         if (globaltimer_ns() > deadline + 1000000000ull) {
-          if (tid == 0) atomicOr(&J.misc->timeout, 1u);
+          load_expired = true;
           break;
         }
       }
-      phase ^= 1u;
     }
-    __syncthreads();
+    if (__syncthreads_or(load_expired)) {
+      // The tile did not arrive in time.  The block stops: it reports the
+      // timeout, gives the copy in flight one more bounded wait so that
+      // nothing still writes into its shared memory when it exits, and
+      // neither re-arms the barrier nor reuses the tile buffer.  The tiles
+      // behind this one time out in their look-backs.
+      if (tid == 0) atomicOr(&J.misc->timeout, 1u);
+      const uint64_t last = globaltimer_ns() + 1000000000ull;
+      while (!mbar_try_wait(&H->mbar, phase) && globaltimer_ns() < last) {
+      }
+      return;
+    }
+    if (bulk > 0) phase ^= 1u;
     PP_PHASE(1);
     PP_WMARK();
 

@@ -252,14 +252,17 @@ class Parser:
         n = data.numel()
         if rows_cap is None:
             rows_cap = max(1024, n // 16)
-        out = self.allocate(rows_cap, [max(n, 1)] * len(self.types), device=data.device)
-        self.parse_into(data, out, stream=stream)
-        res = out.result()
-        if res.status == _abi.E_CAPACITY:
-            caps = [max(int(b), 1) for b in res.values_bytes_needed]
-            out = self.allocate(max(res.rows, 1), caps, device=data.device)
-            self.parse_into(data, out, stream=stream)
+        s = torch.cuda.current_stream(data.device) if stream is None else stream
+        # outputs allocated (zero fill included) and results read back on the parse's stream
+        with torch.cuda.stream(s):
+            out = self.allocate(rows_cap, [max(n, 1)] * len(self.types), device=data.device)
+            self.parse_into(data, out, stream=s)
             res = out.result()
+            if res.status == _abi.E_CAPACITY:
+                caps = [max(int(b), 1) for b in res.values_bytes_needed]
+                out = self.allocate(max(res.rows, 1), caps, device=data.device)
+                self.parse_into(data, out, stream=s)
+                res = out.result()
         return out, res
 
 

@@ -65,6 +65,10 @@ class Server:
         self.waiting.append(req)
 
     def _admit(self) -> list[Request]:
+        """Takes waiting requests while their outputs fit.  Called with the
+        round's stream current, so the outputs (and the zero fill of their
+        result buffers) are allocated on that stream, ordered before its
+        parse."""
         batch = []
         while self.waiting and len(batch) < self.max_batch:
             need = self.waiting[0].out_bytes()
@@ -95,10 +99,11 @@ class Server:
     def step(self) -> int:
         """Admits and launches one round; returns the number of requests launched."""
         self.poll()
-        batch = self._admit()
+        stream = self.streams[self.next_stream]
+        with torch.cuda.stream(stream):
+            batch = self._admit()
         if not batch:
             return 0
-        stream = self.streams[self.next_stream]
         self.next_stream = (self.next_stream + 1) % len(self.streams)
         with torch.cuda.stream(stream):
             parse_batch([(r.parser, r.data, r.out) for r in batch], stream=stream)
@@ -151,8 +156,8 @@ def run_trace_plain(requests: list[Request], offsets_s: np.ndarray, device="cuda
         while i < n and offsets_s[i] <= now:
             r = requests[i]
             r.arrival = t0 + offsets_s[i]
-            r.out = r.parser.allocate(r.rows_cap, r.values_caps, device=device)
-            with torch.cuda.stream(stream):
+            with torch.cuda.stream(stream):  # the outputs' zero fill is ordered before the parse
+                r.out = r.parser.allocate(r.rows_cap, r.values_caps, device=device)
                 r.parser.parse_into(r.data, r.out, stream=stream)
                 ev = torch.cuda.Event()
                 ev.record(stream)

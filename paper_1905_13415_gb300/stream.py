@@ -74,7 +74,8 @@ class StreamParser:
         if self.outs[b] is None:
             nbytes = self.carry + self.part
             rows = max(1024, int(nbytes * self.rows_per_byte))
-            self.outs[b] = self.parser.allocate(rows, [nbytes] * len(self.parser.types), device=self.device)
+            with torch.cuda.stream(self.s_parse):  # zero fill ordered before the parses on s_parse
+                self.outs[b] = self.parser.allocate(rows, [nbytes] * len(self.parser.types), device=self.device)
         return self.outs[b]
 
     def _host_like(self, t: torch.Tensor, n: int) -> torch.Tensor:
@@ -190,9 +191,10 @@ class StreamParser:
     def _checked(self, out: Output, b: int, start: int, length: int, partial: bool):
         res = out.result()
         if res.status == _abi.E_CAPACITY:  # grow this buffer's outputs and parse the partition again
-            self.outs[b] = self.parser.allocate(max(res.rows, 1),
-                                                [max(int(x), 1) for x in res.values_bytes_needed],
-                                                device=self.device)
+            with torch.cuda.stream(self.s_parse):
+                self.outs[b] = self.parser.allocate(max(res.rows, 1),
+                                                    [max(int(x), 1) for x in res.values_bytes_needed],
+                                                    device=self.device)
             self.parser.set_option(_abi.OPT_PARTIAL_INPUT, 1 if partial else 0)
             self.parser.parse_into(self.bufs[b][start:start + length], self.outs[b], stream=self.s_parse)
             torch.cuda.current_stream().wait_stream(self.s_parse)

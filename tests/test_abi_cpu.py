@@ -43,6 +43,21 @@ def test_exports_every_declared_symbol(abi):
     assert declared == set(abi.EXPORTED)
 
 
+def test_header_constants_match_binding(abi):
+    """The binding's copies of the header's numeric constants cannot drift."""
+    text = open(os.path.join(ROOT, "include", "parparaw.h")).read()
+
+    def define(name):
+        m = re.search(r"#define\s+" + name + r"\s+\(?(\d+)u?\s*(?:<<\s*(\d+))?\)?", text)
+        assert m, name
+        return int(m.group(1)) << int(m.group(2) or 0)
+
+    assert define("PP_NOALLOC_SCRATCH_BYTES") == abi.NOALLOC_SCRATCH_BYTES
+    assert define("PP_INFER_MAX_FIELDS") == abi.INFER_MAX_FIELDS
+    assert define("PP_MAX_COLUMNS") == abi.MAX_COLUMNS
+    assert define("PP_MAX_STRING_COLUMNS") == abi.MAX_STRING_COLUMNS
+
+
 def test_status_strings(abi):
     for code in range(-9, 1):
         assert abi.status_string(code) and abi.status_string(code) != "unknown status"
