@@ -120,6 +120,21 @@ def records(workload: str, seed: int, row0: int, nrows: int):
     return bytes(raw[: rl.value]), recs
 
 
+def record_bytes(workload: str, seed: int, row0: int, nrows: int) -> np.ndarray:
+    """The raw bytes of records [row0, row0 + nrows) alone (no truth
+    returned); they equal that slice of the whole generated input."""
+    cap = max(1 << 16, nrows * 2048)
+    while True:
+        raw = np.empty(cap, np.uint8)
+        truth = np.empty(cap, np.uint8)
+        rl, tl = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        rc = lib().synth_records(WORKLOADS[workload], seed, row0, nrows, raw.ctypes.data, cap,
+                                 ctypes.byref(rl), truth.ctypes.data, cap, ctypes.byref(tl))
+        if rc == 0:
+            return raw[: rl.value]
+        cap = max(rl.value, tl.value) + 1
+
+
 def batch_plan(n: int, total: int, seed: int, lo: int = 1 << 10, hi: int = 64 << 20, sigma: float = 2.0):
     """Sizes and workloads of a batch: log-normal sizes clipped to [lo, hi] and
     rescaled so they sum to about `total`; half CSV ('mixed'), half web logs."""

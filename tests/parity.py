@@ -51,3 +51,36 @@ def assert_same(got_host: dict, res, ref, rows_cap: int | None = None, what=""):
 def first_diff(a, b):
     idx = np.nonzero(a != b)[0]
     return None if len(idx) == 0 else (int(idx[0]), a[idx[0]], b[idx[0]])
+
+
+def _bits(bm: np.ndarray, r0: int, r1: int) -> np.ndarray:
+    """Bits [r0, r1) of an LSB-first bitmap, one uint8 per bit."""
+    return np.unpackbits(bm, bitorder="little")[r0:r1]
+
+
+def assert_rows_equal(out, r0: int, r1: int, ref, what=""):
+    """Rows [r0, r1) of a device Output equal, element by element, the
+    oracle's parse of exactly those records (string offsets compared relative
+    to the first row's; validity and row_valid bit by bit)."""
+    import torch
+
+    n = r1 - r0
+    assert ref.rows == n, (what, ref.rows, n)
+    b0, b1 = r0 // 8, (r1 + 7) // 8
+    for c, col in enumerate(ref.columns):
+        if col.type == O.SKIP:
+            continue
+        if col.offsets is not None:
+            offs = out.offsets[c][r0: r1 + 1].cpu().numpy()
+            assert np.array_equal(offs - offs[0], col.offsets[: n + 1]), (what, c, "offsets")
+            vals = out.values[c][int(offs[0]): int(offs[-1])].cpu().numpy()
+            assert np.array_equal(vals, col.values[: int(col.offsets[n])]), (what, c, "bytes")
+        else:
+            got = out.values[c][r0:r1].cpu().numpy()
+            assert np.array_equal(got.view(np.uint8), col.values[:n].view(np.uint8)), \
+                (what, c, "values", first_diff(got, col.values[:n]))
+        vb = out.validity[c][b0:b1].cpu().numpy()
+        assert np.array_equal(_bits(vb, r0 - 8 * b0, r1 - 8 * b0), _bits(col.validity, 0, n)), (what, c, "validity")
+    rv = out.row_valid[b0:b1].cpu().numpy()
+    assert np.array_equal(_bits(rv, r0 - 8 * b0, r1 - 8 * b0), _bits(ref.row_valid, 0, n)), (what, "row_valid")
+    torch.cuda.synchronize()
