@@ -277,6 +277,85 @@ pp_status parparaw_batch_launch(pp_batch* batch, void* stream);
 /* Frees the batch (cudaFree: call it once its launches have completed). */
 void parparaw_batch_destroy(pp_batch* batch);
 
+/* End-to-end streaming from host memory (Sec. 4.4, "End-to-End Streaming"):
+ * the input lives in host memory and is parsed in partitions while the next
+ * partition is copied in and the previous one's columns are copied out.
+ * A streamer owns two device input buffers (each a carry-over region in
+ * front of a partition), two sets of device output columns, a pinned result
+ * block and three CUDA streams (copy in, parse, copy out).  Each partition
+ * but the last is parsed as a partial input (PP_OPT_PARTIAL_INPUT): its bytes
+ * after the last record delimiter are an incomplete record, which the device
+ * reports as `consumed`; they are copied on the device into the carry-over
+ * region of the other buffer and parsed again at the start of the next
+ * partition, which restarts in the DFA's start state (this holds for formats
+ * whose record delimiter leads back to the start state).  The host waits for
+ * each partition's result only to size its copy-out and the carry-over; the
+ * copies of the neighbouring partitions run meanwhile. */
+typedef struct pp_streamer pp_streamer;
+
+/* Creates a streamer for `parser` (its DFA, schema and options are copied;
+ * PP_OPT_SKIP_RECORDS applies to the first partition).  partition_bytes: input
+ * bytes copied in per partition (> 0); carry_bytes: the longest incomplete
+ * record carried over (0 = partition_bytes).  Allocates the device buffers
+ * (cudaMalloc; output columns sized for one record per 16 input bytes, grown
+ * on demand), pinned host memory for the results, three streams and events
+ * on the current device.  *out is released with parparaw_stream_destroy. */
+pp_status parparaw_stream_create(const pp_parser* parser, uint64_t partition_bytes, uint64_t carry_bytes,
+                                 pp_streamer** out);
+
+/* The columns of one partition, in the caller's host arena.  cols[c] holds
+ * host pointers (NULL for PP_SKIP columns): STRING values (values_cap =
+ * bytes) and int64 offsets [rows + 1] starting at 0; numeric values [rows];
+ * validity bitmaps (rows + 7) / 8 bytes, LSB first.  The partition's rows are
+ * rows [row0, row0 + rows) of the whole input's parse. */
+typedef struct pp_host_partition {
+  int64_t rows;
+  int64_t row0;
+  uint64_t input_offset; /* first input byte of the partition (its carry-over included) */
+  uint64_t input_bytes;  /* bytes parsed for it */
+  pp_column cols[PP_MAX_COLUMNS];
+  uint8_t* row_valid;
+} pp_host_partition;
+
+/* Outcome of a streamed parse.
+ *   status               PP_OK, or the status of the first partition that
+ *                        failed (PP_E_INVALID_INPUT, PP_E_UNTERMINATED,
+ *                        PP_E_TIMEOUT) -- the partitions before it, and that
+ *                        partition's rows before the failure, are output; or
+ *                        PP_E_CAPACITY when the arena is too small, or
+ *                        PP_E_UNSUPPORTED when a record is longer than the
+ *                        carry-over region
+ *   num_partitions       partitions written to parts
+ *   rows, n_rejected     over the partitions written
+ *   first_invalid_offset in the whole input, or -1
+ *   arena_bytes          arena bytes used; on PP_E_CAPACITY, the bytes that
+ *                        the partitions so far plus the one that did not fit
+ *                        need */
+typedef struct pp_stream_result {
+  int32_t status;
+  uint32_t num_partitions;
+  int64_t rows;
+  int64_t n_rejected;
+  int64_t first_invalid_offset;
+  uint64_t arena_bytes;
+} pp_stream_result;
+
+/* Parses `len` bytes of host memory at `input` (pinned memory lets the
+ * copies run at full speed; pageable memory works but each copy then
+ * blocks) into columns carved from the host arena [arena, arena +
+ * arena_bytes) (64-byte aligned pieces; pinned for speed).  `parts` (host,
+ * max_parts entries, at least ceil(len / partition_bytes)) receives one entry
+ * per partition.  Synchronous: returns once every partition's columns are in
+ * the arena and the streamer's streams are idle.  Calls on one streamer must
+ * not overlap.  Returns PP_E_ARG for bad arguments (too few parts entries
+ * included), PP_E_NOMEM / PP_E_CUDA for allocation and CUDA errors; the
+ * parse outcome is in *result. */
+pp_status parparaw_stream_parse(pp_streamer* streamer, const uint8_t* input, uint64_t len, uint8_t* arena,
+                                uint64_t arena_bytes, pp_host_partition* parts, uint64_t max_parts,
+                                pp_stream_result* result);
+
+void parparaw_stream_destroy(pp_streamer* streamer);
+
 /* Size of the fixed device scratch behind parparaw_parse_noalloc. */
 #define PP_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -24,7 +24,8 @@ EXPORTED = ["parparaw_create", "parparaw_destroy", "parparaw_set_option", "parpa
             "parparaw_parse", "parparaw_parse_batch", "parparaw_set_kernel_events",
             "parparaw_status_string", "parparaw_parse_noalloc", "parparaw_batch_create",
             "parparaw_batch_launch", "parparaw_batch_destroy", "parparaw_infer",
-            "parparaw_skip_rows_scratch_bytes", "parparaw_skip_rows"]
+            "parparaw_skip_rows_scratch_bytes", "parparaw_skip_rows", "parparaw_stream_create",
+            "parparaw_stream_parse", "parparaw_stream_destroy"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -75,6 +76,17 @@ class pp_parser_info(ctypes.Structure):
 
 
 RESULT_BYTES = ctypes.sizeof(pp_parse_result)
+
+
+class pp_host_partition(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("row0", ctypes.c_int64), ("input_offset", ctypes.c_uint64),
+                ("input_bytes", ctypes.c_uint64), ("cols", pp_column * MAX_COLUMNS), ("row_valid", ctypes.c_void_p)]
+
+
+class pp_stream_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("num_partitions", ctypes.c_uint32), ("rows", ctypes.c_int64),
+                ("n_rejected", ctypes.c_int64), ("first_invalid_offset", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_uint64)]
 
 INFER_MAX_FIELDS = 256
 TYPE_NONE = 0xFF
@@ -137,6 +149,14 @@ def load():
     L.parparaw_skip_rows.argtypes = [vp, ctypes.c_uint64, vp, ctypes.c_uint64, ctypes.c_uint8, vp, vp, vp,
                                      ctypes.c_uint64, vp]
     L.parparaw_skip_rows.restype = ctypes.c_int
+    L.parparaw_stream_create.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(vp)]
+    L.parparaw_stream_create.restype = ctypes.c_int
+    L.parparaw_stream_parse.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.c_uint64,
+                                        ctypes.POINTER(pp_host_partition), ctypes.c_uint64,
+                                        ctypes.POINTER(pp_stream_result)]
+    L.parparaw_stream_parse.restype = ctypes.c_int
+    L.parparaw_stream_destroy.argtypes = [vp]
+    L.parparaw_stream_destroy.restype = None
     L.parparaw_status_string.argtypes = [ctypes.c_int]
     L.parparaw_status_string.restype = ctypes.c_char_p
     _lib = L

@@ -12,17 +12,9 @@
 
 #include "pp_device.cuh"
 #include "pp_launch.h"
+#include "pp_parser.h"
 #include "pp_types.h"
 
-struct pp_parser {
-  pp::Tables tab;
-  uint32_t types[PP_MAX_COLUMNS];
-  int tile_config = 0;
-  uint64_t timeout_ns = 2000000000ull;
-  int64_t grid_limit = 0;
-  uint32_t first_item = 0;
-  cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
-};
 
 namespace pp {
 namespace {

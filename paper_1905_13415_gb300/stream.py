@@ -1,205 +1,126 @@
-"""End-to-end streaming parse of host-resident input (Sec. 4.4).
+"""End-to-end streaming parse of host-resident input (Sec. 4.4): binding of
+parparaw_stream_create / _parse / _destroy.
 
-The input is split into partitions.  Two device input buffers alternate:
-while partition k is parsed from one, partition k+1 is copied into the other
-and the columns of partition k-1 are copied back to the host, on three
-streams.  Each buffer keeps a carry-over region in front of its partition:
-the incomplete last record of partition k (the bytes after its last record
-delimiter, reported by the device as `consumed`) is copied there so that it
-is parsed at the start of partition k+1.  Partitions are parsed with
-PP_OPT_PARTIAL_INPUT; the last one as a whole input.  The output is one
-Arrow-like record batch per partition, in host memory.
-
-The carry-over restarts each partition in the DFA's start state, which holds
-for formats whose record delimiters lead back to the start state (both
-formats shipped here).
+The library owns the pipeline: two device input buffers with a carry-over
+region each, two sets of device output columns and three CUDA streams
+(copy in, parse, copy out).  While partition k is parsed, partition k+1 is
+copied in and the columns of partition k-1 are copied out to a host arena;
+the incomplete record at the end of a partition is carried over on the device
+to the front of the next one.  This module only marshals arguments and wraps
+the partitions' host columns as tensors.
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 
 import torch
 
 from . import _abi
-from .parser import Output, Parser, ParparawError
+from .parser import Parser, ParparawError
+
+_TORCH_OF = {_abi.INT32: torch.int32, _abi.DATE_D: torch.int32, _abi.INT64: torch.int64,
+             _abi.TIMESTAMP_S: torch.int64, _abi.TIMESTAMP_CLF: torch.int64, _abi.FLOAT64: torch.float64}
 
 
 @dataclasses.dataclass
 class Partition:
     rows: int
+    row0: int                        # first row of the whole parse in this partition
+    input_offset: int                # first input byte parsed for it (carry-over included)
     nbytes: int                      # input bytes parsed (carry-over included)
-    columns: list                    # per column: dict of host tensors
+    columns: list                    # per column: dict of host tensors (views of the arena)
     row_valid: torch.Tensor
 
 
 class HostArena:
-    """One pinned host buffer that the columns of a stream's partitions are
-    carved from, so that a parse allocates no pinned memory per partition.
-    Reusable across parses: the partitions of a parse stay valid until the
-    arena's next parse (reset)."""
+    """A pinned host buffer that the partitions' columns are carved from (by
+    the library).  The partitions of a parse stay valid until the arena's
+    next parse."""
 
     def __init__(self, nbytes: int):
-        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=True)
-        self.used = 0
+        self.buf = torch.empty(max(int(nbytes), 64), dtype=torch.uint8, pin_memory=True)
 
-    def reset(self) -> None:
-        self.used = 0
-
-    def take(self, n: int, dtype) -> torch.Tensor | None:
+    def view(self, ptr: int, n: int, dtype) -> torch.Tensor:
         size = torch.empty(0, dtype=dtype).element_size()
-        start = (self.used + 63) & ~63
-        end = start + max(n, 1) * size
-        if end > self.buf.numel():
-            return None
-        self.used = end
-        return self.buf[start:end].view(dtype)
+        off = ptr - self.buf.data_ptr()
+        assert 0 <= off and off + n * size <= self.buf.numel()
+        return self.buf[off: off + n * size].view(dtype)
 
 
 class StreamParser:
+    """Streams pinned host input through the parser in partitions of
+    `partition_bytes`; a record may be at most `carry_bytes` long."""
+
     def __init__(self, parser: Parser, partition_bytes: int = 256 << 20, carry_bytes: int | None = None,
-                 rows_per_byte: float = 1 / 16, device="cuda"):
+                 device="cuda", **_unused):
         self.parser = parser
         self.part = int(partition_bytes)
-        self.carry = int(carry_bytes or partition_bytes)
-        self.device = torch.device(device)
-        self.rows_per_byte = rows_per_byte
-        self.bufs = [torch.empty(self.carry + self.part, dtype=torch.uint8, device=self.device) for _ in range(2)]
-        self.s_h2d = torch.cuda.Stream(device=self.device)
-        self.s_parse = torch.cuda.Stream(device=self.device)
-        self.s_d2h = torch.cuda.Stream(device=self.device)
-        self.outs = [None, None]
-        self.arena = None
+        self._lib = _abi.load()
+        self.handle = ctypes.c_void_p()
+        with torch.cuda.device(torch.device(device)):
+            rc = self._lib.parparaw_stream_create(parser.handle, self.part, int(carry_bytes or 0),
+                                                  ctypes.byref(self.handle))
+        if rc != _abi.OK:
+            raise ParparawError(rc, "parparaw_stream_create")
 
-    def _out(self, b: int) -> Output:
-        if self.outs[b] is None:
-            nbytes = self.carry + self.part
-            rows = max(1024, int(nbytes * self.rows_per_byte))
-            with torch.cuda.stream(self.s_parse):  # zero fill ordered before the parses on s_parse
-                self.outs[b] = self.parser.allocate(rows, [nbytes] * len(self.parser.types), device=self.device)
-        return self.outs[b]
+    def close(self) -> None:
+        if self.handle:
+            self._lib.parparaw_stream_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
 
-    def _host_like(self, t: torch.Tensor, n: int) -> torch.Tensor:
-        if self.arena is not None:
-            x = self.arena.take(n, t.dtype)
-            if x is not None:
-                return x
-        return torch.empty(max(n, 1), dtype=t.dtype, pin_memory=True)
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
-    def _copy_back(self, out: Output, res, nbytes_in: int, done: torch.cuda.Event) -> Partition:
-        _host_like = self._host_like
-        rows = res.rows
-        nb = (rows + 7) // 8
-        cols = []
-        with torch.cuda.stream(self.s_d2h):
-            for c, t in enumerate(out.types):
-                col = {}
-                if t == _abi.SKIP:  # not selected: nothing to copy
-                    cols.append({"values": None, "offsets": None, "validity": None})
-                    continue
-                if t == _abi.STRING:
-                    nbytes = int(res.values_bytes_needed[c])
-                    col["values"] = _host_like(out.values[c], nbytes)
-                    col["values"][:nbytes].copy_(out.values[c][:nbytes], non_blocking=True)
-                    col["offsets"] = _host_like(out.offsets[c], rows + 1)
-                    col["offsets"][:rows + 1].copy_(out.offsets[c][:rows + 1], non_blocking=True)
-                else:
-                    col["values"] = _host_like(out.values[c], rows)
-                    col["values"][:rows].copy_(out.values[c][:rows], non_blocking=True)
-                col["validity"] = _host_like(out.validity[c], nb)
-                col["validity"][:nb].copy_(out.validity[c][:nb], non_blocking=True)
-                cols.append(col)
-            rv = _host_like(out.row_valid, nb)
-            rv[:nb].copy_(out.row_valid[:nb], non_blocking=True)
-            done.record(self.s_d2h)
-        return Partition(rows, nbytes_in, cols, rv)
-
-    def parse(self, host: torch.Tensor, arena: HostArena | None = None) -> list[Partition]:
-        """Parses the pinned uint8 host tensor; returns the partitions' columns,
-        in pinned host memory (carved from `arena` when given: then they stay
-        valid until the arena's next use)."""
-        self.arena = arena
-        if arena is not None:
-            arena.reset()
+    def parse_raw(self, host: torch.Tensor, arena: HostArena):
+        """One parparaw_stream_parse call: (pp_stream_result, partitions array)."""
         n = host.numel()
         nparts = max(1, (n + self.part - 1) // self.part)
-        ev = lambda: torch.cuda.Event()  # noqa: E731
-        h2d_done = [ev(), ev()]
-        parse_done = [ev(), ev()]
-        d2h_done = [ev(), ev()]
-        carry_done = ev()
-        for e in (*parse_done, *d2h_done, carry_done):
-            e.record(self.s_parse)
+        parts = (_abi.pp_host_partition * nparts)()
+        res = _abi.pp_stream_result()
+        rc = self._lib.parparaw_stream_parse(self.handle, host.data_ptr() if n else None, n,
+                                             arena.buf.data_ptr(), arena.buf.numel(), parts, nparts,
+                                             ctypes.byref(res))
+        if rc != _abi.OK:
+            raise ParparawError(rc, "parparaw_stream_parse")
+        return res, parts
 
-        def h2d(k):
-            b = k % 2
-            lo = k * self.part
-            ln = min(self.part, n - lo)
-            self.s_h2d.wait_event(carry_done)  # the carry-over out of this buffer is taken
-            with torch.cuda.stream(self.s_h2d):
-                self.bufs[b][self.carry:self.carry + ln].copy_(host[lo:lo + ln], non_blocking=True)
-                h2d_done[b].record(self.s_h2d)
-            return ln
-
-        skip = self.parser.skip_records  # Sec. 4.3: they are all in the first partition
-        try:
-            results: list[Partition] = []
-            lens = [0] * nparts
-            lens[0] = h2d(0)
-            prev = None  # (buffer, start, length, Output) of partition k-1
-            for k in range(nparts):
-                b = k % 2
-                last = k + 1 == nparts
-                carry_len = 0
-                if prev is not None:
-                    pb, pstart, plen, pout = prev
-                    parse_done[pb].synchronize()
-                    res = self._checked(pout, pb, pstart, plen, partial=True)
-                    results.append(self._copy_back(self.outs[pb], res, plen, d2h_done[pb]))
-                    if k == 1 and skip and res.rows == 0:
-                        raise ParparawError(_abi.E_UNSUPPORTED, "the skipped records reach past the first partition")
-                    carry_len = plen - res.consumed
-                    if carry_len > self.carry:
-                        raise ParparawError(_abi.E_UNSUPPORTED, "a record is longer than the carry-over region")
-                    self.s_parse.wait_event(h2d_done[b])
-                    if carry_len:
-                        with torch.cuda.stream(self.s_parse):
-                            self.bufs[b][self.carry - carry_len:self.carry].copy_(
-                                self.bufs[pb][pstart + res.consumed:pstart + plen], non_blocking=True)
-                    carry_done.record(self.s_parse)
-                start = self.carry - carry_len
-                length = carry_len + lens[k]
-                self.s_parse.wait_event(h2d_done[b])
-                self.s_parse.wait_event(d2h_done[b])  # this buffer's previous copy-back
-                out = self._out(b)
-                self.parser.set_option(_abi.OPT_PARTIAL_INPUT, 0 if last else 1)
-                self.parser.set_option(_abi.OPT_SKIP_RECORDS, skip if k == 0 else 0)
-                self.parser.parse_into(self.bufs[b][start:start + length], out, stream=self.s_parse)
-                parse_done[b].record(self.s_parse)
-                if not last:
-                    lens[k + 1] = h2d(k + 1)  # overlaps with this partition's parse
-                prev = (b, start, length, out)
-            pb, pstart, plen, pout = prev
-            parse_done[pb].synchronize()
-            res = self._checked(pout, pb, pstart, plen, partial=False)
-            results.append(self._copy_back(self.outs[pb], res, plen, d2h_done[pb]))
-            torch.cuda.synchronize()
-            return results
-        finally:
-            self.parser.set_option(_abi.OPT_PARTIAL_INPUT, 0)
-            self.parser.set_option(_abi.OPT_SKIP_RECORDS, skip)
-
-    def _checked(self, out: Output, b: int, start: int, length: int, partial: bool):
-        res = out.result()
-        if res.status == _abi.E_CAPACITY:  # grow this buffer's outputs and parse the partition again
-            with torch.cuda.stream(self.s_parse):
-                self.outs[b] = self.parser.allocate(max(res.rows, 1),
-                                                    [max(int(x), 1) for x in res.values_bytes_needed],
-                                                    device=self.device)
-            self.parser.set_option(_abi.OPT_PARTIAL_INPUT, 1 if partial else 0)
-            self.parser.parse_into(self.bufs[b][start:start + length], self.outs[b], stream=self.s_parse)
-            torch.cuda.current_stream().wait_stream(self.s_parse)
-            self.s_parse.synchronize()
-            res = self.outs[b].result()
+    def parse(self, host: torch.Tensor, arena: HostArena | None = None) -> list[Partition]:
+        """Parses the pinned uint8 host tensor; returns the partitions' columns
+        as views of `arena` (a pinned arena sized on demand when None)."""
+        own = arena is None
+        if own:
+            arena = HostArena(2 * host.numel() + (1 << 20))
+        while True:
+            res, parts = self.parse_raw(host, arena)
+            if res.status == _abi.E_CAPACITY and own:
+                arena = HostArena(max(2 * arena.buf.numel(), int(res.arena_bytes * 1.25)))
+                continue
+            break
         if res.status != _abi.OK:
-            raise ParparawError(res.status, "partition")
-        return res
+            raise ParparawError(res.status, "streamed parse")
+        out = []
+        types = self.parser.types
+        for k in range(res.num_partitions):
+            p = parts[k]
+            rows, nb = p.rows, (p.rows + 7) // 8
+            cols = []
+            for c, t in enumerate(types):
+                hc = p.cols[c]
+                if t == _abi.SKIP:
+                    cols.append({"values": None, "offsets": None, "validity": None})
+                    continue
+                col = {"validity": arena.view(hc.validity, nb, torch.uint8)}
+                if t == _abi.STRING:
+                    col["values"] = arena.view(hc.values, hc.values_cap, torch.uint8)
+                    col["offsets"] = arena.view(hc.offsets, rows + 1, torch.int64)
+                else:
+                    col["values"] = arena.view(hc.values, rows, _TORCH_OF[t])
+                    col["offsets"] = None
+                cols.append(col)
+            out.append(Partition(rows, p.row0, p.input_offset, p.input_bytes, cols,
+                                 arena.view(p.row_valid, nb, torch.uint8)))
+        return out

@@ -156,3 +156,62 @@ def test_autotune_picks_a_measured_config(pp):
     best, times = autotune([(p, data, out)], reps=2)
     assert best in times and all(t > 0 for t in times.values())
     assert p.info().tile_bytes > 0
+
+
+def test_stream_entry_outcomes(pp):
+    """parparaw_stream_parse through the C ABI: partition offsets and rows,
+    an invalid byte in a later partition (offset in the whole input), an
+    unterminated end, a record longer than the carry-over region, an arena
+    that is too small, and skipped records (first partition only)."""
+    from paper_1905_13415_gb300 import _abi
+    from paper_1905_13415_gb300.stream import HostArena, StreamParser
+
+    raw, _ = synth.records("mixed", 44, 0, 3000)
+    schema = synth.SCHEMAS["mixed"]
+    p = pp.Parser(pp.formats.by_name("csv"), schema, tile_config=2)
+    host = torch.frombuffer(bytearray(raw), dtype=torch.uint8).pin_memory()
+    sp = StreamParser(p, partition_bytes=20_000, carry_bytes=20_000)
+    parts = sp.parse(host)
+    ref = oracle_parse("csv", schema, raw)
+    assert sum(x.rows for x in parts) == ref.rows
+    row0 = 0
+    for x in parts:  # partitions tile the rows and the input
+        assert x.row0 == row0
+        row0 += x.rows
+    assert parts[0].input_offset == 0 and parts[-1].input_offset + parts[-1].nbytes == len(raw)
+
+    # an invalid byte (a quote inside an unquoted field) in a later partition
+    bad = bytearray(raw)
+    pos = raw.index(b"\n", 50_000) + 2
+    while bad[pos - 1] in b'",\n' or bad[pos] in b'",\n':
+        pos += 1
+    bad[pos] = ord('"')
+    ref_bad = oracle_parse("csv", schema, bytes(bad))
+    assert ref_bad.status == O.E_INVALID_INPUT
+    res, parts_arr = sp.parse_raw(torch.frombuffer(bad, dtype=torch.uint8).pin_memory(), HostArena(4 * len(raw)))
+    assert res.status == _abi.E_INVALID_INPUT and res.first_invalid_offset == ref_bad.first_invalid_offset
+    assert res.rows == ref_bad.rows  # every record before the invalid byte
+
+    # an unterminated quote at the end of the input
+    unterminated = raw + b'1,"abc'
+    res, _ = sp.parse_raw(torch.frombuffer(bytearray(unterminated), dtype=torch.uint8).pin_memory(),
+                          HostArena(4 * len(raw)))
+    assert res.status == _abi.E_UNTERMINATED
+
+    # a record longer than the carry-over region
+    long_rec = raw + b'1,"' + b"x" * 50_000 + b'",2,3.5,2020-01-01T00:00:00,a,2020-01-01T00:00:00,b\n' + raw
+    res, _ = sp.parse_raw(torch.frombuffer(bytearray(long_rec), dtype=torch.uint8).pin_memory(),
+                          HostArena(8 * len(long_rec)))
+    assert res.status == _abi.E_UNSUPPORTED
+
+    # an arena too small: PP_E_CAPACITY with the size the partitions so far need
+    res, _ = sp.parse_raw(host, HostArena(4096))
+    assert res.status == _abi.E_CAPACITY and res.arena_bytes > 4096 and res.num_partitions == 0
+    sp.close()
+
+    # skipped records leave the first partition only
+    p2 = pp.Parser(pp.formats.by_name("csv"), schema, tile_config=2, skip_records=5)
+    sp2 = StreamParser(p2, partition_bytes=20_000, carry_bytes=20_000)
+    parts2 = sp2.parse(host)
+    assert sum(x.rows for x in parts2) == ref.rows - 5
+    sp2.close()
