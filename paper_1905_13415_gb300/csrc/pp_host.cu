@@ -441,6 +441,24 @@ extern "C" pp_status parparaw_create(const pp_dfa* dfa, const pp_symbol_groups* 
     }
     T.trans_run[g] = row;
   }
+  // one-lookup steps of the re-simulation (see Tables::step)
+  for (uint32_t r = 0; r < 2; ++r)
+    for (uint32_t g = 0; g < PP_MAX_GROUPS; ++g)
+      for (uint32_t s0 = 0; s0 < PP_MAX_STATES; ++s0) {
+        const uint32_t inv = dfa->invalid_state;
+        uint32_t s1 = s0;
+        bool slow = false;
+        if (r) {
+          s1 = (tca >> (8 * s0)) & 0xFF;
+          const uint32_t e_ca = T.emit[groups->catch_all];
+          const uint32_t tag0 = (e_ca >> (2 * s0)) & 3u, tagr = (e_ca >> (2 * s1)) & 3u;
+          slow = tag0 != PP_TAG_DATA || tagr != PP_TAG_DATA || (s0 != inv && s1 == inv);
+        }
+        const uint32_t ns = (T.trans[g] >> (8 * s1)) & 0xFF;
+        const uint32_t tag = (T.emit[g] >> (2 * s1)) & 3u;
+        const bool enters_inv = s1 != inv && ns == inv;
+        T.step[r][g][s0] = static_cast<uint8_t>(ns | (tag << 3) | (enters_inv ? kStepInv : 0) | (slow ? kStepSlow : 0));
+      }
   bool idem = true;
   for (uint32_t s = 0; s < S; ++s) {
     const uint32_t once = (tca >> (8 * s)) & 0xFF;

@@ -13,6 +13,12 @@ struct Tables {
   uint64_t trans_run[PP_MAX_GROUPS];   // a catch-all run, then the group
   uint32_t emit[PP_MAX_GROUPS];        // bits [2s, 2s+1] = tag of (group, s)
   uint32_t rep[PP_MAX_SYMBOLS];        // symbol byte replicated into 4 lanes
+  // Re-simulation step of one special symbol of group g read in state s,
+  // after a run of catch-all symbols (r = 1) or directly (r = 0):
+  // step[r][g][s] = next state | tag << 3 | kStepInv (the symbol's transition
+  // enters the invalid state) | kStepSlow (r = 1 and the run is not all data
+  // or enters the invalid state: re-simulated byte by byte).
+  uint8_t step[2][PP_MAX_GROUPS][PP_MAX_STATES];
   uint8_t col_type[PP_MAX_COLUMNS];
   uint8_t str_slot[PP_MAX_COLUMNS];    // string column -> slot, else 0xFF
   uint8_t num_slot[PP_MAX_COLUMNS];    // numeric column -> slot, else 0xFF
@@ -87,6 +93,9 @@ struct Launch {
 
 static_assert(sizeof(Job) % 8 == 0 && sizeof(Tables) % 4 == 0 && sizeof(Col) % 8 == 0,
               "descriptors are copied in 4- and 8-byte words");
+
+constexpr uint8_t kStepInv = 0x20;
+constexpr uint8_t kStepSlow = 0x40;
 
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagInc = 2ull << 62;

@@ -65,7 +65,9 @@ class Inference:
 class Output:
     """Caller-owned device buffers for one parse (Arrow-like columns)."""
 
-    def __init__(self, types, rows_cap: int, values_caps, device):
+    def __init__(self, types, rows_cap: int, values_caps, device, result_buf: torch.Tensor | None = None):
+        """``result_buf``: RESULT_BYTES of device memory for the parse result
+        (a slice of a larger block, say); allocated here when None."""
         self.types = list(types)
         self.rows_cap = int(rows_cap)
         self.device = device
@@ -86,7 +88,8 @@ class Output:
                 self.offsets.append(None)
             self.validity.append(torch.empty(max(nbits, 1), dtype=torch.uint8, device=device))
         self.row_valid = torch.empty(max(nbits, 1), dtype=torch.uint8, device=device)
-        self.result_buf = torch.zeros(_abi.RESULT_BYTES, dtype=torch.uint8, device=device)
+        self.result_buf = (torch.zeros(_abi.RESULT_BYTES, dtype=torch.uint8, device=device) if result_buf is None
+                           else result_buf)
         self.values_caps = [int(values_caps[c]) if t == _abi.STRING else 0 for c, t in enumerate(self.types)]
         self.desc = _abi.pp_columns()
         self.desc.num_columns = len(self.types)
@@ -222,10 +225,10 @@ class Parser:
         except Exception:
             pass
 
-    def allocate(self, rows_cap: int, values_caps, device="cuda") -> Output:
+    def allocate(self, rows_cap: int, values_caps, device="cuda", result_buf: torch.Tensor | None = None) -> Output:
         if isinstance(values_caps, int):
             values_caps = [values_caps] * len(self.types)
-        return Output(self.types, rows_cap, values_caps, torch.device(device))
+        return Output(self.types, rows_cap, values_caps, torch.device(device), result_buf)
 
     def parse_into(self, data: torch.Tensor, out: Output, nbytes: int | None = None, stream=None) -> None:
         """Enqueues the parse of `data` (uint8, CUDA) into `out` on `stream`."""

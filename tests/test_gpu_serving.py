@@ -89,6 +89,33 @@ def test_server_result_alone_equals_result_in_the_mix(pp):
         assert np.array_equal(mixed["row_valid"], host["row_valid"])
 
 
+def test_server_sizes_requests_and_retries_on_capacity(pp):
+    """Requests sized from their length only: inputs with more records than
+    one per 16 bytes report PP_E_CAPACITY and are admitted again with the
+    exact sizes; every result equals the plain parse."""
+    from paper_1905_13415_gb300.serve import Request, Server
+
+    p = pp.Parser(pp.formats.by_name("csv"), ["string", "int32"])
+    raws = [b"".join(b"%d,%d\n" % (i % 7, i) for i in range(n)) for n in (10, 300, 2000, 5000)]
+    raws += [synth.records("mixed", 90 + i, 0, 50)[0] for i in range(4)]
+    ps = [p] * 4 + [pp.Parser(pp.formats.by_name("csv"), synth.SCHEMAS["mixed"])] * 4
+    reqs = [Request(i, q, _dev(raw)) for i, (q, raw) in enumerate(zip(ps, raws))]
+    server = Server(arena_bytes=1 << 26, streams=2, max_batch=3, keep_outputs=True)
+    for r in reqs:
+        server.submit(r)
+    server.drain()
+    torch.cuda.synchronize()
+    assert server.retries >= 2  # the short-record inputs outgrow the estimate
+    for r, raw, q in zip(reqs, raws, ps):
+        out, res = q.parse(_dev(raw))
+        got = r.out.result()
+        assert got.status == res.status == 0 and got.rows == res.rows == r.rows
+        a, b = r.out.to_host(got.rows), out.to_host(res.rows)
+        for ca, cb in zip(a["columns"], b["columns"]):
+            assert np.array_equal(ca["values"].view(np.uint8), cb["values"].view(np.uint8))
+            assert np.array_equal(ca["validity"], cb["validity"])
+
+
 def test_partial_input_mode(pp):
     raw, _ = synth.records("mixed", 21, 0, 500)
     schema = synth.SCHEMAS["mixed"]
