@@ -58,15 +58,19 @@ __device__ __forceinline__ int conv_integer(const uint8_t* t, int n, bool is32, 
   const bool neg = t[0] == '-';
   if (neg) i = 1;
   if (i >= n) return kConvFail;
-  const uint64_t lim = is32 ? (neg ? 2147483648ull : 2147483647ull)
-                            : (neg ? 9223372036854775808ull : 9223372036854775807ull);
+  // leading zeros add nothing; up to 19 significant digits accumulate in 64
+  // bits without overflow (10^19 < 2^64), and more exceed every limit
+  while (i + 1 < n && t[i] == '0') ++i;
+  if (n - i > 19) return kConvFail;
   uint64_t m = 0;
   for (; i < n; ++i) {
     const uint32_t d = static_cast<uint32_t>(t[i]) - '0';
     if (d > 9u) return kConvFail;
-    if (m > (lim - d) / 10) return kConvFail;
     m = m * 10 + d;
   }
+  const uint64_t lim = is32 ? (neg ? 2147483648ull : 2147483647ull)
+                            : (neg ? 9223372036854775808ull : 9223372036854775807ull);
+  if (m > lim) return kConvFail;
   const uint64_t v = neg ? (0ull - m) : m;
   *out = is32 ? static_cast<uint64_t>(static_cast<uint32_t>(v)) : v;
   return kConvOk;

@@ -41,6 +41,7 @@
 // Every spin (mbarrier, look-back) is bounded by %globaltimer and reports
 // PP_E_TIMEOUT instead of hanging.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 
 #include "pp_convert.cuh"
@@ -101,15 +102,22 @@ struct TileShape {
   static_assert(T < 32768, "tile positions are 15-bit field-list entries");
 };
 
-// A long string field queued for a warp-wide copy: destination, first data
-// byte and end in the tile, data bytes, whether they are contiguous.
-struct LongField {
+// A piece of a long string field, copied by whichever warp is free; 16
+// bytes, so that a warp reads it with one shared-memory vector load.
+//   dst  contiguous piece: destination of its first byte; gapped: the
+//        field's destination
+//   x0   first tile position of the piece
+//   len  contiguous piece: bytes; gapped: tile positions it spans
+//   fd   gapped: the field's first data position (ranks count from it);
+//        kContiguousPiece for a contiguous piece
+//   nb   gapped: the field's data bytes (the destination's extent)
+struct alignas(16) Piece {
   uint8_t* dst;
-  uint16_t fd, e;
-  uint32_t nb;
-  uint32_t contiguous;
+  uint16_t x0, len, fd, nb;
 };
-constexpr uint32_t kLongQ = 64;  // long fields queued per round (more are copied where found)
+static_assert(sizeof(Piece) == 16, "one 16-byte load per piece");
+constexpr uint16_t kContiguousPiece = 0xFFFF;
+constexpr uint32_t kMaxPieces = 128;  // pieces queued per round (fields that do not fit are copied where found)
 constexpr uint32_t kPiece = 512;  // queued long fields are copied in pieces of this many tile bytes
 
 struct SmemHead {
@@ -137,10 +145,11 @@ struct SmemHead {
   uint32_t rr_next;
   uint32_t round_tot[PP_MAX_STRING_COLUMNS];   // string bytes of the round per slot
   uint32_t round_base[PP_MAX_STRING_COLUMNS];  // string bytes of the earlier rounds
-  uint32_t nlong;
+  uint32_t npieces;       // pieces claimed in the queue
+  uint32_t npieces_ok;    // pieces written (a prefix of the queue)
   uint32_t w2_g;         // threads per record of the round's step (2)
   uint32_t piece_next;   // the next long-field piece to copy
-  LongField longs[kLongQ];
+  alignas(16) Piece pieces[kMaxPieces];  // read with 16-byte loads
 #ifdef PP_PHASE_TIMING
   long long ph_cycles[32];  // profiling builds only
   unsigned long long w_max[8], w_sum[8];
@@ -148,6 +157,8 @@ struct SmemHead {
   Job jd;                  // the current job and its columns, staged from the
   Col cd[PP_MAX_COLUMNS];  // launch parameters / global memory once per job
 };
+
+static_assert(offsetof(SmemHead, pieces) % 16 == 0, "16-byte loads of the piece queue");
 
 template <class Shape>
 struct SmemLayout {
@@ -512,7 +523,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       H->job = j;
       H->tile_last_rd = 0;
       H->eof_rd = 0;
-      H->nlong = 0;
+      H->npieces = H->npieces_ok = 0;
     }
     if (tid < PP_MAX_STRING_COLUMNS) H->round_base[tid] = 0;
     __syncthreads();
@@ -728,11 +739,16 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       BitIter<MW> it(spec);
       for (int p = it.next(); p >= 0; p = it.next()) {
         const int rs = max(prev + 1, lo);
-        if (rs < p) run(rs, p);
         const uint32_t g = TB.group_of[chunk[p]];
-        const uint32_t tag = (TB.emit[g] >> (2 * s)) & 3u;
-        const uint32_t ns = vget(TB.trans[g], s);
-        if (s != inv && ns == inv && inv_pos < 0) inv_pos = p;
+        // one lookup for the catch-all run before the symbol (if any) and the
+        // symbol itself; runs that are not all data take the byte-exact path
+        uint32_t st = TB.step[rs < p ? 1 : 0][g][s];
+        if (st & kStepSlow) {
+          run(rs, p);
+          st = TB.step[0][g][s];
+        }
+        const uint32_t tag = (st >> 3) & 3u;
+        if ((st & kStepInv) && inv_pos < 0) inv_pos = p;
         // a special symbol is never data unless its tag says so
 #pragma unroll
         for (int w = 0; w < MW; ++w) {
@@ -741,12 +757,12 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           else if (tag == PP_TAG_FIELD) fm[w] |= bit;
           else if (tag == PP_TAG_RECORD) rm[w] |= bit;
         }
-        s = ns;
+        s = st & 7u;
         prev = p;
       }
       {
         const int rs = max(prev + 1, lo);
-        if (rs < hi) run(rs, hi);
+        if (rs < hi && (TB.step[1][0][s] & kStepSlow)) run(rs, hi);  // else all data
       }
       if (inv_pos >= 0)
         atomicMin(&J.misc->first_invalid,
@@ -936,13 +952,14 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       const uint32_t b1 = min(tid * per + per, nwin);
       const uint32_t b0 = min(max(tid * per, first_kept(r0.rr0, nwin)), b1);
       for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
-      uint32_t dprev = data_before(b0 == 0 ? r0.prev_pos + 1 : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu));
-      for (uint32_t g = b0; g < b1; ++g) {
+      int eprev = b0 == 0 ? r0.prev_pos : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu);
+      for (uint32_t g = b0; g < b1; ++g) {  // data bytes are counted for string fields only
         const uint32_t fe = s_fe[g];
-        const uint32_t de = data_before(static_cast<int>(fe & 0x7FFFu));
+        const int e = static_cast<int>(fe & 0x7FFFu);
         const uint32_t c = (fe >> 16) & 0xFFu;
-        if (c < C && TB.str_slot[c] != 0xFF) s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(de - dprev);
-        dprev = de;
+        if (c < C && TB.str_slot[c] != 0xFF)
+          s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(data_before(e) - data_before(eprev + 1));
+        eprev = e;
       }
       // block scan of the per-slot counts, two 16-bit slots per word
       const uint32_t K = (NS + 1) / 2;
@@ -990,7 +1007,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       if (tid == 0) {
         H->prev_pos = H->next_prev_pos;
         H->rr0 = H->rr_next;
-        H->nlong = 0;
+        H->npieces = H->npieces_ok = 0;
       }
       if (tid < static_cast<int>(NS)) H->round_base[tid] += H->round_tot[tid];
       __syncthreads();
@@ -1107,21 +1124,34 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         const uint32_t b1 = min(tid * per + per, nwin);
         const uint32_t b0 = min(max(tid * per, first_kept(rr0, nwin)), b1);
         for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = static_cast<uint16_t>(s_cnt[k * NT + tid] + H->round_base[k]);
-        int eprev = b0 == 0 ? prev_pos : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu);
-        uint32_t dprev = data_before(eprev + 1);
-        for (uint32_t i = 0; i < per; ++i) {  // the same trip count in every lane (warp-wide copies)
-          const uint32_t g = b0 + i;
+        // the entries of the share with work: string fields, and records that
+        // end with the wrong number of fields (rare); the others need nothing
+        static_assert(Shape::B / 4 <= 64, "a share has at most 64 entries");
+        uint64_t work = 0;
+        for (uint32_t g = b0; g < b1; ++g) {
+          const uint32_t fe = s_fe[g];
+          const uint32_t c = (fe >> 16) & 0xFFu;
+          const bool str = NS > 0 && c < C && TB.str_slot[c] != 0xFF;
+          const bool rej = !INFER && (fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead);
+          if (str || rej) work |= 1ull << (g - b0);
+        }
+        const int trips = __reduce_max_sync(0xffffffffu, static_cast<unsigned>(__popcll(work)));
+        for (int it = 0; it < trips; ++it) {  // the same trip count in every lane (warp-wide copies)
           bool is_long = false, contiguous = true;
-          int fd = 0;
+          int fd = 0, e_cur = 0;
           uint32_t nb = 0;
           uint8_t* gdst = nullptr;
-          if (g < b1) {
+          if (work) {
+          const uint32_t g = b0 + static_cast<uint32_t>(__ffsll(static_cast<long long>(work)) - 1);
+          work &= work - 1;
+          const int eprev = g == 0 ? prev_pos : static_cast<int>(s_fe[g - 1] & 0x7FFFu);
           const uint32_t fe = s_fe[g];
           const int e = static_cast<int>(fe & 0x7FFFu);
+          e_cur = e;
           const uint32_t c = (fe >> 16) & 0xFFu;
           if (NS > 0) {
-            const uint32_t de = data_before(e);
-            if (c < C && TB.str_slot[c] != 0xFF) {
+            if (c < C && TB.str_slot[c] != 0xFF) {  // data bytes are counted for string fields only
+              const uint32_t de = data_before(e), dprev = data_before(eprev + 1);
               const uint32_t slot = TB.str_slot[c];
               const uint16_t run = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (de - dprev));
               s_cnt[slot * NT + tid] = run;
@@ -1134,11 +1164,21 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
                   gdst = static_cast<uint8_t*>(cols[c].values) + off;
                   fd = first_data(eprev + 1, e);
                   contiguous = data_before(fd + static_cast<int>(nb)) == dprev + nb;
-                  if (nb > kLongField) {  // queued for the block, else (queue full) copied by this warp below
-                    const uint32_t q = atomicAdd(&H->nlong, 1u);
-                    if (q < kLongQ) {
-                      H->longs[q] = LongField{gdst, static_cast<uint16_t>(fd), static_cast<uint16_t>(e), nb,
-                                              contiguous ? 1u : 0u};
+                  if (nb > kLongField) {  // queued in pieces for the block, else (queue full) copied by this warp below
+                    const uint32_t span = contiguous ? nb : static_cast<uint32_t>(e - fd);
+                    const uint32_t np = (span + kPiece - 1) / kPiece;
+                    const uint32_t q = atomicAdd(&H->npieces, np);
+                    if (q + np <= kMaxPieces) {  // the pieces written form a prefix of the queue
+                      for (uint32_t k = 0; k < np; ++k) {
+                        const uint32_t x0 = static_cast<uint32_t>(fd) + k * kPiece;
+                        H->pieces[q + k] =
+                            contiguous ? Piece{gdst + k * kPiece, static_cast<uint16_t>(x0),
+                                               static_cast<uint16_t>(min(kPiece, nb - k * kPiece)), kContiguousPiece, 0}
+                                       : Piece{gdst, static_cast<uint16_t>(x0),
+                                               static_cast<uint16_t>(min(kPiece, static_cast<uint32_t>(e) - x0)),
+                                               static_cast<uint16_t>(fd), static_cast<uint16_t>(nb)};
+                      }
+                      atomicMax(&H->npieces_ok, q + np);
                     } else {
                       is_long = true;
                     }
@@ -1152,9 +1192,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
                 }
               }
             }
-            dprev = de;
           }
-          eprev = e;
           if (!INFER && (fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
             // the record ends with the wrong number of fields: reject it and
             // give the missing columns their defaults
@@ -1188,7 +1226,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
               if (__shfl_sync(0xffffffffu, contiguous, src)) {
                 warp_copy_out(ldst, s_tile + lfd, static_cast<int>(lnb), lane);
               } else {  // data bytes with gaps: each lane places the bytes it holds by their rank
-                const int le = __shfl_sync(0xffffffffu, eprev, src);  // the field's end
+                const int le = __shfl_sync(0xffffffffu, e_cur, src);  // the field's end
                 const uint32_t d0 = data_before(lfd);
                 for (int u = lfd / B; u * B < le; ++u) {
                   for (int x = u * B + lane; x < (u + 1) * B; x += 32) {
@@ -1209,47 +1247,30 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       __syncthreads();
       PP_PHASE(10);
       PP_WMARK();
-      // the queued long fields in pieces of kPiece tile bytes, spread over
-      // all warps (a whole field per warp leaves one warp copying a long
-      // text while the block waits for it)
+      // the queued pieces of long fields, taken by whichever warp is free (a
+      // whole field per warp leaves one warp copying a long text while the
+      // block waits for it)
       {
-        const uint32_t nl = min(H->nlong, kLongQ);
-        auto pieces = [&](uint32_t i) -> uint32_t {
-          if (i >= nl) return 0u;
-          const LongField& lf = H->longs[i];
-          const uint32_t span = lf.contiguous ? lf.nb : static_cast<uint32_t>(lf.e - lf.fd);
-          return (span + kPiece - 1) / kPiece;
-        };
-        const auto add = [](uint32_t a, uint32_t b) { return a + b; };
-        static_assert(kLongQ == 64, "two queue entries per lane");
-        // inclusive piece counts over the queue: entry `lane` in s_lo, entry
-        // 32 + lane in s_hi
-        const uint32_t s_lo = warp_inclusive_scan(pieces(lane), add, lane);
-        const uint32_t s_hi = warp_inclusive_scan(pieces(lane + 32), add, lane) + __shfl_sync(0xffffffffu, s_lo, 31);
-        const uint32_t total = __shfl_sync(0xffffffffu, s_hi, 31);
-        // pieces taken in turn by whichever warp is free; a warp takes its
-        // next piece before it copies the one in hand
-        uint32_t p = 0;
-        if (lane == 0) p = atomicAdd(&H->piece_next, 1u);
-        p = __shfl_sync(0xffffffffu, p, 0);
-        for (uint32_t pn = 0; p < total; p = __shfl_sync(0xffffffffu, pn, 0)) {
-          if (lane == 0) pn = atomicAdd(&H->piece_next, 1u);
-          // the entry holding piece p follows every entry whose pieces end at or before p
-          const uint32_t i = __popc(__ballot_sync(0xffffffffu, s_lo <= p)) + __popc(__ballot_sync(0xffffffffu, s_hi <= p));
-          const uint32_t before = __shfl_sync(0xffffffffu, i <= 32 ? s_lo : s_hi, (i + 31) & 31);
-          const uint32_t k = p - (i == 0 ? 0u : before);  // piece k of entry i
-          const LongField lf = H->longs[i];
-          const int x0 = static_cast<int>(lf.fd + k * kPiece);
-          if (lf.contiguous) {
-            warp_copy_out(lf.dst + k * kPiece, s_tile + x0, static_cast<int>(min(kPiece, lf.nb - k * kPiece)), lane);
+        const uint32_t total = H->npieces_ok;
+        for (;;) {
+          uint32_t p = 0;
+          if (lane == 0) p = atomicAdd(&H->piece_next, 1u);
+          p = __shfl_sync(0xffffffffu, p, 0);
+          if (p >= total) break;
+          const uint4 raw = reinterpret_cast<const uint4*>(H->pieces)[p];
+          uint8_t* dst = reinterpret_cast<uint8_t*>((static_cast<uint64_t>(raw.y) << 32) | raw.x);
+          const int x0 = static_cast<int>(raw.z & 0xFFFFu), len = static_cast<int>(raw.z >> 16);
+          const uint32_t fd = raw.w & 0xFFFFu, nb = raw.w >> 16;
+          if (fd == kContiguousPiece) {
+            warp_copy_out(dst, s_tile + x0, len, lane);
           } else {  // data bytes with gaps (a doubled quote, say): its runs of data bytes one by one
-            const uint32_t d0 = data_before(lf.fd);
-            const int x1 = min(x0 + static_cast<int>(kPiece), static_cast<int>(lf.e));
+            const uint32_t d0 = data_before(static_cast<int>(fd));
+            const int x1 = x0 + len;
             for (int a = first_data(x0, x1); a < x1;) {
               const int z = first_gap(a, x1);
               const uint32_t rank = data_before(a) - d0;
-              if (rank >= lf.nb) break;
-              warp_copy_out(lf.dst + rank, s_tile + a, min(z - a, static_cast<int>(lf.nb - rank)), lane);
+              if (rank >= nb) break;
+              warp_copy_out(dst + rank, s_tile + a, min(z - a, static_cast<int>(nb - rank)), lane);
               a = first_data(z, x1);
             }
           }

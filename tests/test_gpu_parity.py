@@ -130,6 +130,21 @@ def test_rejects_and_nulls(pp):
         assert_same(got, res, oracle_parse("csv", schema, raw), what=cfg)
 
 
+def test_integer_edge_cases(pp):
+    """Leading zeros, the int32 / int64 limits and one past them, 19- and
+    20-digit values, signs and stray bytes, against the oracle."""
+    vals = ["0", "-0", "00000000000000000000000042", "2147483647", "2147483648", "-2147483648",
+            "-2147483649", "9223372036854775807", "9223372036854775808", "-9223372036854775808",
+            "-9223372036854775809", "99999999999999999999", "9999999999999999999",
+            "0000000000000000000009223372036854775807", "-00000000000000000000000000000001", "-", "+5",
+            "1a", " 1", "", "007"]
+    raw = "".join(f"{v},{v}\n" for v in vals).encode()
+    schema = ["int32", "int64"]
+    for cfg in (1, 2, 10):
+        got, res = run(pp, "csv", schema, raw, cfg)
+        assert_same(got, res, oracle_parse("csv", schema, raw), what=cfg)
+
+
 def test_capacity(pp):
     raw, _ = synth.records("mixed", 3, 0, 1000)
     schema = synth.SCHEMAS["mixed"]
