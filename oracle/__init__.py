@@ -41,6 +41,8 @@ class _Format(ctypes.Structure):
         ("start_state", ctypes.c_uint8),
         ("invalid_state", ctypes.c_uint8),
         ("accept_mask", ctypes.c_uint32),
+        ("catch_all", ctypes.c_uint8),
+        ("unit", ctypes.c_uint8),
     ]
 
 
@@ -91,6 +93,10 @@ def lib():
                                       ctypes.c_uint8, ctypes.c_uint8, ctypes.c_uint32]
         L.ppo_format_init.restype = ctypes.c_int
         L.ppo_state_vector.argtypes = [ctypes.POINTER(_Format), ctypes.c_void_p, ctypes.c_size_t, u8p]
+        L.ppo_state_vector_at.argtypes = [ctypes.POINTER(_Format), ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_size_t, ctypes.c_size_t, u8p]
+        L.ppo_format_set_utf16le.argtypes = [ctypes.POINTER(_Format)]
+        L.ppo_format_set_utf16le.restype = None
         L.ppo_compose.argtypes = [ctypes.c_uint32, u8p, u8p, u8p]
         L.ppo_trace.argtypes = [ctypes.POINTER(_Format), ctypes.c_void_p, ctypes.c_size_t,
                                 ctypes.c_void_p, ctypes.c_void_p]
@@ -138,6 +144,7 @@ class Format:
     start_state: int
     invalid_state: int
     accept_mask: int
+    utf16le: bool = False  # Sec. 4.2: read UTF-16LE code units (surrogate pairs as one symbol)
 
     def __post_init__(self):
         self._c = _Format()
@@ -150,6 +157,13 @@ class Format:
                                    self.invalid_state, self.accept_mask)
         if rc != 0:
             raise ValueError("malformed DFA tables")
+        if self.utf16le:
+            lib().ppo_format_set_utf16le(ctypes.byref(self._c))
+
+    def as_utf16le(self) -> "Format":
+        """The same DFA reading UTF-16LE code units (Sec. 4.2)."""
+        return Format(self.num_states, self.num_groups, self.next, self.emit, self.symbols, self.groups,
+                      self.catch_all, self.start_state, self.invalid_state, self.accept_mask, True)
 
     def group_of(self, b: int) -> int:
         return int(self._c.group_of[b])
@@ -225,6 +239,16 @@ def state_vector(fmt: Format, chunk: bytes) -> np.ndarray:
     buf = np.frombuffer(bytes(chunk), dtype=np.uint8)
     lib().ppo_state_vector(ctypes.byref(fmt._c), buf.ctypes.data, len(buf),
                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return out[: fmt.num_states].copy()
+
+
+def state_vector_at(fmt: Format, data: bytes, begin: int, end: int) -> np.ndarray:
+    """Vector of the chunk data[begin:end] of a whole input (Sec. 4.2: the
+    symbols that start in the chunk)."""
+    out = np.zeros(MAX_STATES, np.uint8)
+    buf = np.frombuffer(bytes(data), dtype=np.uint8)
+    lib().ppo_state_vector_at(ctypes.byref(fmt._c), buf.ctypes.data, len(buf), begin, end,
+                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     return out[: fmt.num_states].copy()
 
 

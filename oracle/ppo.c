@@ -58,7 +58,56 @@ int ppo_format_init(ppo_format* f, uint32_t S, uint32_t G, const uint8_t* next,
   f->start_state = start_state;
   f->invalid_state = invalid_state;
   f->accept_mask = accept_mask;
+  f->catch_all = catch_all;
+  f->unit = 1;
   return 0;
+}
+
+void ppo_format_set_utf16le(ppo_format* f) { f->unit = 2; }
+
+/* ------------------------------------ Sec. 4.2: variable-length symbols */
+
+static uint32_t unit16(const uint8_t* in, size_t i) { return (uint32_t)in[i] | ((uint32_t)in[i + 1] << 8); }
+static int is_high(uint32_t u) { return u >= 0xD800 && u <= 0xDBFF; }
+static int is_low(uint32_t u) { return u >= 0xDC00 && u <= 0xDFFF; }
+
+/* Length in bytes and group of the symbol that starts at in[i]. */
+static size_t symbol_at(const ppo_format* f, const uint8_t* in, size_t len, size_t i, uint8_t* group) {
+  if (f->unit == 1) {
+    *group = f->group_of[in[i]];
+    return 1;
+  }
+  if (i + 2 > len) { /* a lone trailing byte: not a code unit, read as the catch-all */
+    *group = f->catch_all;
+    return 1;
+  }
+  const uint32_t u = unit16(in, i);
+  if (is_high(u) && i + 4 <= len && is_low(unit16(in, i + 2))) {
+    *group = f->catch_all; /* a code point beyond U+FFFF */
+    return 4;
+  }
+  *group = u <= 0xFF ? f->group_of[u] : f->catch_all;
+  return 2;
+}
+
+void ppo_state_vector_at(const ppo_format* f, const uint8_t* in, size_t len, size_t begin, size_t end,
+                         uint8_t out[PPO_MAX_STATES]) {
+  /* the chunk's first symbol: its first code unit, unless that unit is the
+   * low half of a pair whose high half is the previous code unit */
+  size_t first = begin;
+  if (f->unit == 2 && begin >= 2 && begin + 2 <= len && is_low(unit16(in, begin)) &&
+      is_high(unit16(in, begin - 2)))
+    first = begin + 2;
+  for (uint32_t i = 0; i < PPO_MAX_STATES; ++i) out[i] = (uint8_t)i;
+  for (uint32_t i = 0; i < f->num_states; ++i) {
+    uint8_t s = (uint8_t)i;
+    for (size_t k = first; k < end;) {
+      uint8_t g;
+      k += symbol_at(f, in, len, k, &g);
+      s = f->next[g][s];
+    }
+    out[i] = s;
+  }
 }
 
 /* ------------------------------------------------- Sec. 3.1: vectors and o */
@@ -339,8 +388,22 @@ static void end_field(parse_state* p) {
       p->field_end[c] = (int64_t)p->values[c].n;
     } else {
       uint64_t v = 0;
-      p->field_conv[c] = (uint8_t)ppo_convert(p->types[c], p->num, p->num_len, &v);
-      p->field_value[c] = v;
+      const uint8_t* text = p->num;
+      size_t n = p->num_len;
+      uint8_t narrow[PPO_NUMERIC_MAX_LEN + 1];
+      int ok = 1;
+      if (p->f->unit == 2 && n <= PPO_NUMERIC_MAX_LEN) { /* UTF-16LE text: ASCII code points only */
+        ok = n % 2 == 0;
+        for (size_t k = 0; ok && k < n / 2; ++k) {
+          const uint32_t u = unit16(p->num, 2 * k);
+          ok = u < 0x80;
+          narrow[k] = (uint8_t)u;
+        }
+        text = narrow;
+        n /= 2;
+      }
+      p->field_conv[c] = ok ? (uint8_t)ppo_convert(p->types[c], text, n, &v) : PPO_CONV_FAIL;
+      p->field_value[c] = ok ? v : 0;
     }
   }
   p->num_len = 0;
@@ -405,21 +468,25 @@ int ppo_parse_skip(const ppo_format* f, const uint32_t* types, uint32_t C, const
   int64_t first_invalid = -1;
   size_t since_record = 0; /* bytes read since the last record delimiter */
   uint8_t s = f->start_state;
-  for (size_t i = 0; i < len; ++i) {
-    uint8_t g = f->group_of[in[i]];
+  for (size_t i = 0; i < len;) {
+    uint8_t g;
+    const size_t n = symbol_at(f, in, len, i, &g); /* one symbol (Sec. 4.2): n bytes */
     uint8_t tag = f->emit[g][s];
     uint8_t nxt = f->next[g][s];
     if (f->invalid_state != PPO_NO_STATE && nxt == f->invalid_state &&
         s != f->invalid_state && first_invalid < 0)
       first_invalid = (int64_t)i;
     switch (tag) {
-      case PPO_DATA: on_data(p, in[i]); break;
+      case PPO_DATA:
+        for (size_t k = 0; k < n; ++k) on_data(p, in[i + k]);
+        break;
       case PPO_FIELD: end_field(p); break;
       case PPO_RECORD: end_field(p); end_record(p); break;
       default: break; /* control symbol: not part of any field */
     }
-    since_record = (tag == PPO_RECORD) ? 0 : since_record + 1;
+    since_record = (tag == PPO_RECORD) ? 0 : since_record + n;
     s = nxt;
+    i += n;
   }
   int accepting = (f->accept_mask >> s) & 1u;
   if (since_record > 0 && accepting) {

@@ -68,6 +68,8 @@ typedef struct ppo_format {
   uint8_t start_state;
   uint8_t invalid_state;                     /* PPO_NO_STATE if none */
   uint32_t accept_mask;                      /* bit s: state s accepting at end */
+  uint8_t catch_all;                         /* group of every symbol not listed */
+  uint8_t unit;                              /* Sec. 4.2: 1 = byte symbols; 2 = UTF-16LE */
 } ppo_format;
 
 typedef struct ppo_result {
@@ -93,6 +95,21 @@ int ppo_format_init(ppo_format* f, uint32_t S, uint32_t G, const uint8_t* next,
                     const uint8_t* emit, uint32_t nsym, const uint8_t* symbols,
                     const uint8_t* groups, uint8_t catch_all, uint8_t start_state,
                     uint8_t invalid_state, uint32_t accept_mask);
+
+/* Sec. 4.2, variable-length symbols: the format reads UTF-16LE code units
+ * instead of bytes.  A symbol is a code unit, or a surrogate pair (a high
+ * surrogate followed by a low one) read as one symbol; code points up to
+ * U+00FF take the group that the byte of the same value has, every other one
+ * the catch-all group.  A symbol's tag applies to all of its bytes; numeric
+ * fields convert when every code point of their text is ASCII. */
+void ppo_format_set_utf16le(ppo_format* f);
+
+/* Sec. 4.2 with Sec. 3.1: the state-transition vector of the chunk
+ * in[begin, end) of a whole input in[0, len): the DFA reads the symbols that
+ * start in the chunk (the last one may end past it); a chunk whose first code
+ * unit completes a surrogate pair begun in the previous chunk skips it. */
+void ppo_state_vector_at(const ppo_format* f, const uint8_t* in, size_t len, size_t begin, size_t end,
+                         uint8_t out[PPO_MAX_STATES]);
 
 /* Sec. 3.1: state-transition vector of a chunk. out[i] = state reached after
  * reading the chunk when the DFA starts in state i (one DFA run per state). */

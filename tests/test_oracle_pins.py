@@ -457,3 +457,111 @@ def test_skip_rows_is_not_skip_records():
     assert (a.rows, a.field(0, 1), a.field(1, 1)) == (b.rows, b.field(0, 1), b.field(1, 1)) == (2, b"x\ny", b"z")
     c = O.parse(O.csv6(), [O.INT32, O.STRING], O.skip_rows(raw, [1]))  # leaves 'y",..' : a stray quote
     assert c.status == O.E_INVALID_INPUT
+
+
+# ------------------------------------------------ Sec. 4.2: UTF-16 symbols
+
+_TEXT_ALPHABET = ["a", "b", "z", "1", " ", "é", "ß", "€", "漢", "字", "😀", "🚀", "𝄞"]
+
+
+def _random_utf8_csv(rng, records):
+    """Records of [int32, string, string, float64] whose strings hold
+    multi-byte and astral characters, some quoted with delimiters inside."""
+    lines = []
+    for _ in range(records):
+        def text():
+            s = "".join(rng.choice(_TEXT_ALPHABET) for _ in range(rng.randint(0, 8)))
+            if rng.random() < 0.4:
+                return '"' + s.replace('"', '""') + rng.choice(["", ",", "\n", '""']) + '"'
+            return s
+        lines.append(f"{rng.randint(-99, 999)},{text()},{text()},{rng.randint(0, 999)}.{rng.randint(0, 99):02d}\n")
+    return "".join(lines)
+
+
+def test_utf16_parse_equals_the_utf8_parse_transcoded():
+    """Sec. 4.2 pinned against Python's own codecs: a CSV input parsed as
+    UTF-16LE code units gives the rows, statuses, numbers and validity of the
+    same input parsed as UTF-8 bytes, and each string field's UTF-16LE bytes
+    decode to the same text as its UTF-8 bytes."""
+    rng = random.Random(42)
+    f8, f16 = O.csv6(), O.csv6().as_utf16le()
+    types = [O.INT32, O.STRING, O.STRING, O.FLOAT64]
+    for it in range(40):
+        text = _random_utf8_csv(rng, rng.randint(1, 30))
+        if it % 5 == 4:  # an invalid input: a quote inside an unquoted field
+            cut = rng.randrange(len(text))
+            text = text[:cut] + 'x"' + text[cut:]
+        r8 = O.parse(f8, types, text.encode("utf-8"))
+        r16 = O.parse(f16, types, text.encode("utf-16-le"))
+        assert (r16.status, r16.rows, r16.n_rejected, r16.final_state) == (r8.status, r8.rows, r8.n_rejected,
+                                                                           r8.final_state)
+        if r8.first_invalid_offset >= 0:  # the same code point, counted in each encoding's bytes
+            cp = len(text.encode("utf-8")[: r8.first_invalid_offset].decode("utf-8"))
+            assert r16.first_invalid_offset == len(text[:cp].encode("utf-16-le"))
+        for c, t in enumerate(types):
+            assert np.array_equal(r16.columns[c].validity, r8.columns[c].validity)
+            for r in range(r8.rows):
+                if t == O.STRING:
+                    assert r16.field(r, c).decode("utf-16-le") == r8.field(r, c).decode("utf-8")
+                else:
+                    assert r16.field(r, c) == r8.field(r, c)
+        assert np.array_equal(r16.row_valid, r8.row_valid)
+
+
+def test_utf16_numeric_text_must_be_ascii():
+    f16 = O.csv6().as_utf16le()
+    raw = "12,x\n１２,y\n".encode("utf-16-le")  # the second number uses fullwidth digits
+    r = O.parse(f16, [O.INT32, O.STRING], raw)
+    assert r.rows == 2 and r.n_rejected == 1
+    assert r.field(0, 0) == 12 and not r.valid(1, 0)
+
+
+def test_utf16_chunk_vectors_compose_at_every_split():
+    """Sec. 4.2 with Sec. 3.1: chunk vectors (a chunk skips the low half of a
+    surrogate pair begun in the previous chunk) compose to the whole input's
+    vector at every code-unit boundary, also inside surrogate pairs."""
+    rng = random.Random(7)
+    f16 = O.csv6().as_utf16le()
+    alphabet = [",", "\n", '"', "\r", "a", "é", "😀", "𝄞"]
+    for _ in range(60):
+        text = "".join(rng.choice(alphabet) for _ in range(rng.randint(1, 12)))
+        raw = text.encode("utf-16-le")
+        n = len(raw)
+        whole = O.state_vector_at(f16, raw, 0, n)
+        seq = O.state_vector(O.csv6(), b"")  # identity
+        assert len(whole) == len(seq)
+        for k in range(0, n + 1, 2):
+            a, b = O.state_vector_at(f16, raw, 0, k), O.state_vector_at(f16, raw, k, n)
+            assert np.array_equal(O.compose(a, b), whole), (text, k)
+        for k1 in range(2, n, 2):  # three chunks
+            k2 = min(n, k1 + 2 * rng.randint(1, 3))
+            v = O.compose(O.compose(O.state_vector_at(f16, raw, 0, k1), O.state_vector_at(f16, raw, k1, k2)),
+                          O.state_vector_at(f16, raw, k2, n))
+            assert np.array_equal(v, whole), (text, k1, k2)
+
+
+def test_utf16_whole_vector_is_the_sequential_run():
+    """The whole input's vector is, per start state, the state where the
+    sequential parse of the UTF-8 form ends (the symbol sequences agree)."""
+    rng = random.Random(8)
+    for _ in range(30):
+        text = "".join(rng.choice([",", "\n", '"', "a", "é", "😀"]) for _ in range(rng.randint(1, 15)))
+        v16 = O.state_vector_at(O.csv6().as_utf16le(), text.encode("utf-16-le"), 0, len(text.encode("utf-16-le")))
+        v8 = O.state_vector(O.csv6(), text.encode("utf-8"))
+        assert np.array_equal(v16, v8), text
+
+
+def test_utf16_reads_a_surrogate_pair_as_one_symbol():
+    """With a DFA whose catch-all flips between two states, the final state
+    is the parity of the number of code points (Python's count), not of the
+    code units: a surrogate pair is one symbol (Sec. 4.2)."""
+    nxt = np.array([[1, 0]], np.uint8)  # one group, the catch-all: toggle
+    emt = np.zeros((1, 2), np.uint8)
+    f16 = O.Format(2, 1, nxt, emt, b"", [], 0, 0, 0xFF, 3, True)
+    rng = random.Random(9)
+    for _ in range(50):
+        text = "".join(rng.choice(["a", "é", "😀", "𝄞", "漢"]) for _ in range(rng.randint(0, 9)))
+        raw = text.encode("utf-16-le")
+        assert O.state_vector_at(f16, raw, 0, len(raw))[0] == len(text) % 2, text
+        r = O.parse(f16, [O.STRING], raw)
+        assert r.final_state == len(text) % 2
