@@ -196,12 +196,30 @@ typedef enum pp_option {
                                later tiles' bounded look-back waits expire and
                                the parse reports PP_E_TIMEOUT; the context stays
                                usable.  Outputs of such a parse are undefined. */
-  PP_OPT_SKIP_RECORDS = 6   /* skipping records (Sec. 4.3): the first n records
+  PP_OPT_SKIP_RECORDS = 6,  /* skipping records (Sec. 4.3): the first n records
                                (0 <= n < 2^32, default 0), e.g. a header, are
                                recognised and validated but leave no row, no
                                string bytes, no conversion and no reject; row 0
                                is record n.  result.rows counts the rows left.
                                parparaw_infer skips them too. */
+  PP_OPT_UTF16LE = 7        /* variable-length symbols (Sec. 4.2): 1 = the input
+                               is UTF-16LE code units.  Symbol bytes b of the
+                               symbol groups stand for code points U+00bb; every
+                               other code unit, surrogates included, is in the
+                               catch-all group, and a surrogate pair reads like
+                               one catch-all symbol.  A symbol's tag covers all
+                               of its bytes, string values keep their UTF-16LE
+                               bytes, and numeric text converts when every code
+                               point is ASCII.  Needs an input address and
+                               length that are even (else parparaw_parse
+                               returns PP_E_ARG), and a catch-all transition
+                               that is idempotent with the same tag before and
+                               after it (else PP_E_UNSUPPORTED here): then a
+                               surrogate pair read as two code units parses as
+                               one symbol.  Parses run with tile configurations
+                               0 (10), 1 and 2 (others: PP_E_UNSUPPORTED);
+                               parparaw_infer returns PP_E_UNSUPPORTED for such
+                               parsers.  0 (default) = byte symbols. */
 } pp_option;
 
 typedef struct pp_parser_info {

@@ -19,6 +19,7 @@ TYPE_NAMES = {"string": STRING, "int32": INT32, "int64": INT64, "float64": FLOAT
               "timestamp": TIMESTAMP_S, "date": DATE_D, "timestamp_clf": TIMESTAMP_CLF, "skip": SKIP}
 
 OPT_TILE_CONFIG, OPT_TIMEOUT_MS, OPT_GRID_LIMIT, OPT_PARTIAL_INPUT, OPT_FIRST_ITEM, OPT_SKIP_RECORDS = 1, 2, 3, 4, 5, 6
+OPT_UTF16LE = 7
 
 EXPORTED = ["parparaw_create", "parparaw_destroy", "parparaw_set_option", "parparaw_get_info",
             "parparaw_parse", "parparaw_parse_batch", "parparaw_set_kernel_events",

@@ -16,8 +16,10 @@ import torch
 from . import _abi
 from .parser import Batch
 
-# (config, threads x bytes per thread): the shapes worth timing for throughput
-CANDIDATES = {2: "64x48", 9: "256x96", 10: "448x64", 11: "512x48", 12: "256x112/3"}
+# (config, threads x bytes per thread [blocks per SM]): every shape but the
+# 32-thread test shape
+CANDIDATES = {2: "64x48", 3: "256x112", 4: "128x208", 5: "128x112/4", 6: "128x112/6", 7: "128x48/8",
+              8: "256x80/3", 9: "256x96/3", 10: "448x64", 11: "512x48", 12: "256x112/3"}
 
 
 def time_batch(items, reps: int = 3, warmup: int = 1, stream=None) -> float:

@@ -288,9 +288,11 @@ int g_last_grid = 0, g_last_per_sm = 0;
 #endif
 
 // Launches init, tile and finalize kernels for a prepared launch.
+// units: some job reads UTF-16LE code units (the kernel form that can).
 pp_status run_launch(Launch& L, const ShapeInfo& shape, int nspec, int64_t grid_limit,
                      const pp_parser* timing, cudaStream_t stream, uint32_t max_jobs_y,
-                     uint64_t max_tiles, uint64_t max_words) {
+                     uint64_t max_tiles, uint64_t max_words, bool units) {
+  if (units && shape.units_kernel == nullptr) return PP_E_UNSUPPORTED;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return map_err(e);
@@ -311,7 +313,7 @@ pp_status run_launch(Launch& L, const ShapeInfo& shape, int nspec, int64_t grid_
   L.phase_cycles = g_phase_cycles;
 #endif
   if (L.total_tiles > 0) {
-    const void* kern = shape.kernel(nspec);
+    const void* kern = units ? shape.units_kernel(nspec) : shape.kernel(nspec);
     int per_sm = 0;
     if ((e = kernel_occupancy(kern, shape.threads, shape.smem_bytes, dev, &per_sm)) != cudaSuccess)
       return map_err(e);
@@ -523,6 +525,23 @@ extern "C" pp_status parparaw_set_option(pp_parser* P, pp_option option, int64_t
       if (value < 0 || value > 0xFFFFFFFFll) return PP_E_ARG;
       P->tab.skip_records = static_cast<uint32_t>(value);
       return PP_OK;
+    case PP_OPT_UTF16LE: {
+      if (value != 0 && value != 1) return PP_E_ARG;
+      if (value == 1) {
+        // code units read one at a time parse a surrogate pair as one symbol
+        // when the catch-all transition is idempotent and keeps its tag
+        const Tables& T = P->tab;
+        const uint64_t tca = T.trans[T.catch_all];
+        const uint32_t eca = T.emit[T.catch_all];
+        if (!T.idempotent) return PP_E_UNSUPPORTED;
+        for (uint32_t s0 = 0; s0 < T.num_states; ++s0) {
+          const uint32_t s1 = (tca >> (8 * s0)) & 0xFF;
+          if (((eca >> (2 * s0)) & 3u) != ((eca >> (2 * s1)) & 3u)) return PP_E_UNSUPPORTED;
+        }
+      }
+      P->tab.unit2 = static_cast<uint8_t>(value);
+      return PP_OK;
+    }
     default:
       return PP_E_ARG;
   }
@@ -552,6 +571,7 @@ extern "C" pp_status parparaw_set_kernel_events(pp_parser* P, void* start_event,
 extern "C" pp_status parparaw_infer(const pp_parser* P, const uint8_t* input, uint64_t len,
                                     pp_inference* result, void* stream_) {
   if (P == nullptr || result == nullptr || (input == nullptr && len > 0)) return PP_E_ARG;
+  if (P->tab.unit2) return PP_E_UNSUPPORTED;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   const ShapeInfo shape = shape_for(0);
   if (shape.infer_kernel == nullptr) return PP_E_UNSUPPORTED;
@@ -624,12 +644,26 @@ extern "C" pp_status parparaw_infer(const pp_parser* P, const uint8_t* input, ui
   return st;
 }
 
-extern "C" pp_status parparaw_parse(const pp_parser* P, const uint8_t* input, uint64_t len,
-                                    const pp_columns* out, void* stream_) {
+// UTF-16LE inputs are whole code units at an even address.
+static bool units_ok(const pp_parser* P, const uint8_t* input, uint64_t len) {
+  return !P->tab.unit2 || ((len % 2) == 0 && (reinterpret_cast<uintptr_t>(input) % 2) == 0);
+}
+
+// The scratch (bytes) that one parse of len bytes into rows_cap rows needs.
+size_t pp_parse_scratch_bytes(const pp_parser* P, uint64_t len, uint64_t rows_cap) {
+  const ShapeInfo shape = shape_for(P->tile_config);
+  const uint64_t ntiles = len > 0 ? (15 + len + shape.tile_bytes - 1) / shape.tile_bytes : 0;  // any alignment
+  return plan_scratch(64, ntiles, P->tab.num_str, P->tab.num_num, (rows_cap + 31) / 32 + 1).total;
+}
+
+// parparaw_parse with the scratch either allocated stream-ordered here
+// (scratch == nullptr) or taken from the caller's device block.
+pp_status pp_parse_with_scratch(const pp_parser* P, const uint8_t* input, uint64_t len, const pp_columns* out,
+                                cudaStream_t stream, uint8_t* scratch_block, size_t scratch_cap) {
   if (P == nullptr || (input == nullptr && len > 0)) return PP_E_ARG;
+  if (!units_ok(P, input, len)) return PP_E_ARG;
   pp_status st = check_columns(P, out);
   if (st != PP_OK) return st;
-  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   const ShapeInfo shape = shape_for(P->tile_config);
 
   Launch* Lp = new (std::nothrow) Launch();
@@ -654,11 +688,18 @@ extern "C" pp_status parparaw_parse(const pp_parser* P, const uint8_t* input, ui
     L.cols0[c].values_cap = out->cols[c].values_cap;
   }
   const ScratchPlan plan = plan_scratch(64, J.ntiles, P->tab.num_str, P->tab.num_num, J.bit_words);
-  uint8_t* scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), plan.total, stream);
-  if (e != cudaSuccess) {
-    delete Lp;
-    return map_err(e);
+  uint8_t* scratch = scratch_block;
+  if (scratch_block != nullptr) {
+    if (plan.total > scratch_cap) {
+      delete Lp;
+      return PP_E_UNSUPPORTED;
+    }
+  } else {
+    const cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), plan.total, stream);
+    if (e != cudaSuccess) {
+      delete Lp;
+      return map_err(e);
+    }
   }
   fill_job(J, plan, scratch);
   L.jobs = nullptr;
@@ -669,10 +710,16 @@ extern "C" pp_status parparaw_parse(const pp_parser* P, const uint8_t* input, ui
   L.work_counter = reinterpret_cast<unsigned long long*>(scratch);
   L.first_item = P->first_item;
   L.timeout_ns = P->timeout_ns;
-  st = run_launch(L, shape, nspec_of(P->tab), P->grid_limit, P, stream, 1, J.ntiles, J.bit_words);
-  cudaFreeAsync(scratch, stream);
+  st = run_launch(L, shape, nspec_of(P->tab), P->grid_limit, P, stream, 1, J.ntiles, J.bit_words,
+                  P->tab.unit2 != 0);
+  if (scratch_block == nullptr) cudaFreeAsync(scratch, stream);
   delete Lp;
   return st;
+}
+
+extern "C" pp_status parparaw_parse(const pp_parser* P, const uint8_t* input, uint64_t len,
+                                    const pp_columns* out, void* stream_) {
+  return pp_parse_with_scratch(P, input, len, out, static_cast<cudaStream_t>(stream_), nullptr, 0);
 }
 
 namespace pp {
@@ -689,6 +736,7 @@ struct BatchPlan {
   const pp_parser* first = nullptr;
   ShapeInfo shape;
   int nspec = 4;
+  bool units = false;  // some item reads UTF-16LE code units
   uint64_t total_tiles = 0, max_tiles = 0, max_words = 0;
   size_t off_tables = 0, off_jobs = 0, off_cols = 0, total = 0;
 };
@@ -706,6 +754,7 @@ pp_status plan_batch(const pp_batch_item* items, uint64_t n, BatchPlan* bp) {
   for (uint64_t i = 0; i < n; ++i) {
     const pp_batch_item& it = items[i];
     if (it.parser == nullptr || (it.input == nullptr && it.len > 0)) return PP_E_ARG;
+    if (!units_ok(it.parser, it.input, it.len)) return PP_E_ARG;
     const pp_status st = check_columns(it.parser, it.out);
     if (st != PP_OK) return st;
     auto found = table_index.find(it.parser);
@@ -715,6 +764,7 @@ pp_status plan_batch(const pp_batch_item* items, uint64_t n, BatchPlan* bp) {
       bp->tables.push_back(it.parser->tab);
       table_index[it.parser] = ti;
       bp->nspec = std::max(bp->nspec, nspec_of(it.parser->tab));
+      bp->units = bp->units || it.parser->tab.unit2 != 0;
     } else {
       ti = found->second;
     }
@@ -809,7 +859,7 @@ extern "C" pp_status parparaw_parse_batch(const pp_batch_item* items, uint64_t n
   }
   batch_launch_params(bp, scratch, Lp);
   st = run_launch(*Lp, bp.shape, bp.nspec, bp.first->grid_limit, bp.first, stream,
-                  static_cast<uint32_t>(std::min<uint64_t>(n, 65535)), bp.max_tiles, bp.max_words);
+                  static_cast<uint32_t>(std::min<uint64_t>(n, 65535)), bp.max_tiles, bp.max_words, bp.units);
   cudaFreeAsync(scratch, stream);
   delete Lp;
   return st;
@@ -850,7 +900,8 @@ extern "C" pp_status parparaw_batch_launch(pp_batch* b, void* stream_) {
   const BatchPlan& bp = b->plan;
   return run_launch(*b->launch, bp.shape, bp.nspec, bp.first->grid_limit, bp.first,
                     static_cast<cudaStream_t>(stream_),
-                    static_cast<uint32_t>(std::min<uint64_t>(bp.jobs.size(), 65535)), bp.max_tiles, bp.max_words);
+                    static_cast<uint32_t>(std::min<uint64_t>(bp.jobs.size(), 65535)), bp.max_tiles, bp.max_words,
+                    bp.units);
 }
 
 extern "C" void parparaw_batch_destroy(pp_batch* b) {
@@ -896,6 +947,7 @@ cudaError_t noalloc_scratch_ptr(int dev, uint8_t** out) {
 extern "C" pp_status parparaw_parse_noalloc(const pp_parser* P, const uint8_t* input, uint64_t len,
                                             const pp_columns* out, void* stream_) {
   if (P == nullptr || (input == nullptr && len > 0)) return PP_E_ARG;
+  if (!units_ok(P, input, len)) return PP_E_ARG;
   pp_status st = check_columns(P, out);
   if (st != PP_OK) return st;
   int dev = 0;
@@ -937,5 +989,6 @@ extern "C" pp_status parparaw_parse_noalloc(const pp_parser* P, const uint8_t* i
   // the same launch sequence as parparaw_parse: the init kernel clears
   // everything the tile kernel needs at zero (status words, bitmaps,
   // counters), since the array keeps the previous call's contents
-  return run_launch(L, shape, nspec_of(P->tab), P->grid_limit, P, stream, 1, J.ntiles, J.bit_words);
+  return run_launch(L, shape, nspec_of(P->tab), P->grid_limit, P, stream, 1, J.ntiles, J.bit_words,
+                    P->tab.unit2 != 0);
 }

@@ -473,7 +473,10 @@ __device__ __forceinline__ void store_value(const Col& col, uint32_t type, uint6
 // record's field count and each field's narrowest numeric type are reduced
 // per tile in shared memory (the per-column sums, unused then) and folded into
 // the job's Misc; nothing is written to the columns.
-template <class Shape, int NSPEC, bool INFER = false>
+// UNITS: the form that also reads UTF-16LE code units (Sec. 4.2) for parsers
+// whose tables ask for it; byte-only launches use the form without, whose
+// code has no branch on the symbol width.
+template <class Shape, int NSPEC, bool INFER = false, bool UNITS = false>
 __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const __grid_constant__ Launch L) {
   constexpr int NT = Shape::NT, VPT = Shape::VPT, B = Shape::B, T = Shape::T, MW = Shape::MW;
   using Lay = SmemLayout<Shape>;
@@ -645,6 +648,34 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
 #pragma unroll
       for (int s = 0; s < NSPEC; ++s) rep[s] = TB.rep[s < TB.num_symbols ? s : 0];
       const uint4* src = reinterpret_cast<const uint4*>(chunk);
+      if (UNITS && TB.unit2) {
+        // UTF-16LE code units (Sec. 4.2): the same test on 16-bit lanes
+        // against the symbols' code units 0x00bb; a flag lands on the unit's
+        // first byte
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          const uint4 q = src[v];
+          const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+          uint32_t acc[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            acc[k] = 0;
+#pragma unroll
+            for (int s = 0; s < NSPEC; ++s) {
+              const uint32_t x = wd[k] ^ (rep[s] & 0x00FF00FFu);
+              acc[k] |= (x - 0x00010001u) & ~x;
+            }
+          }
+          if ((acc[0] | acc[1] | acc[2] | acc[3]) & 0x80008000u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t bits4 = ((acc[k] >> 15) & 1u) | ((acc[k] >> 29) & 4u);
+              const int pos = 16 * v + 4 * k;
+              spec[pos >> 6] |= static_cast<uint64_t>(bits4) << (pos & 63);
+            }
+          }
+        }
+      } else
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
         const uint4 q = src[v];
@@ -674,17 +705,23 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
                                         static_cast<int64_t>(T)));
     const int PE = static_cast<int>(v1 - v0);  // end of the tile's bytes
     // ------------------------------------ a2: multi-state simulation
+    // Symbols are W bytes: 1, or 2 for UTF-16LE code units (a code unit above
+    // U+00FF is in the catch-all group).
+    const int W = (UNITS && TB.unit2) ? 2 : 1;
+    auto group_at = [&](int p) -> uint32_t {
+      return (W == 2 && chunk[p + 1] != 0) ? TB.catch_all : TB.group_of[chunk[p]];
+    };
     uint64_t vec = kIdentityVec;
     {
-      int prev = -1;
+      int prev = -W;
       BitIter<MW> it(spec);
       for (int p = it.next(); p >= 0; p = it.next()) {
-        const bool run = max(prev + 1, lo) < p;
-        const uint32_t g = TB.group_of[chunk[p]];
+        const bool run = max(prev + W, lo) < p;
+        const uint32_t g = group_at(p);
         vec = vcompose(vec, run ? TB.trans_run[g] : TB.trans[g]);
         prev = p;
       }
-      if (max(prev + 1, lo) < hi) vec = vcompose(vec, TB.trans[TB.catch_all]);
+      if (max(prev + W, lo) < hi) vec = vcompose(vec, TB.trans[TB.catch_all]);
     }
 
     // ------------------------------------------- a3: o-scan + chain 1
@@ -709,8 +746,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     PP_WMARK();
     uint64_t dm[MW], fm[MW], rm[MW];
 #pragma unroll
-    for (int w = 0; w < MW; ++w) {
-      dm[w] = bit_range(lo - 64 * w, hi - 64 * w) & ~spec[w];  // runs are data unless fixed below
+    for (int w = 0; w < MW; ++w) {  // runs are data unless fixed below (a symbol's bytes in one word)
+      dm[w] = bit_range(lo - 64 * w, hi - 64 * w) & ~(spec[w] | (W == 2 ? spec[w] << 1 : 0ull));
       fm[w] = rm[w] = 0;
     }
     {
@@ -719,7 +756,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       const uint32_t e_ca = TB.emit[ca];
       const uint64_t t_ca = TB.trans[ca];
       uint32_t s = s_start;
-      int prev = -1, inv_pos = -1;
+      int prev = -W, inv_pos = -1;
       auto run = [&](int rs, int re) {
         const uint32_t s1 = vget(t_ca, s);
         const uint32_t tag0 = (e_ca >> (2 * s)) & 3u, tagr = (e_ca >> (2 * s1)) & 3u;
@@ -727,8 +764,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         if ((tag0 | tagr) != PP_TAG_DATA) {  // rare: a run that is not all data
 #pragma unroll
           for (int w = 0; w < MW; ++w) {
-            const uint64_t b0 = bit_range(rs - 64 * w, rs + 1 - 64 * w);
-            const uint64_t br = bit_range(rs + 1 - 64 * w, re - 64 * w);
+            const uint64_t b0 = bit_range(rs - 64 * w, rs + W - 64 * w);  // the run's first symbol
+            const uint64_t br = bit_range(rs + W - 64 * w, re - 64 * w);
             dm[w] &= ~((tag0 != PP_TAG_DATA ? b0 : 0) | (tagr != PP_TAG_DATA ? br : 0));
             fm[w] |= (tag0 == PP_TAG_FIELD ? b0 : 0) | (tagr == PP_TAG_FIELD ? br : 0);
             rm[w] |= (tag0 == PP_TAG_RECORD ? b0 : 0) | (tagr == PP_TAG_RECORD ? br : 0);
@@ -738,8 +775,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       };
       BitIter<MW> it(spec);
       for (int p = it.next(); p >= 0; p = it.next()) {
-        const int rs = max(prev + 1, lo);
-        const uint32_t g = TB.group_of[chunk[p]];
+        const int rs = max(prev + W, lo);
+        const uint32_t g = group_at(p);
         // one lookup for the catch-all run before the symbol (if any) and the
         // symbol itself; runs that are not all data take the byte-exact path
         uint32_t st = TB.step[rs < p ? 1 : 0][g][s];
@@ -749,11 +786,12 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         }
         const uint32_t tag = (st >> 3) & 3u;
         if ((st & kStepInv) && inv_pos < 0) inv_pos = p;
-        // a special symbol is never data unless its tag says so
+        // a special symbol is never data unless its tag says so; delimiters
+        // are marked at their first byte
 #pragma unroll
         for (int w = 0; w < MW; ++w) {
           const uint64_t bit = (p >> 6) == w ? (1ull << (p & 63)) : 0ull;
-          if (tag == PP_TAG_DATA) dm[w] |= bit;
+          if (tag == PP_TAG_DATA) dm[w] |= bit | (W == 2 ? bit << 1 : 0ull);
           else if (tag == PP_TAG_FIELD) fm[w] |= bit;
           else if (tag == PP_TAG_RECORD) rm[w] |= bit;
         }
@@ -761,7 +799,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         prev = p;
       }
       {
-        const int rs = max(prev + 1, lo);
+        const int rs = max(prev + W, lo);
         if (rs < hi && (TB.step[1][0][s] & kStepSlow)) run(rs, hi);  // else all data
       }
       if (inv_pos >= 0)
@@ -787,9 +825,9 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       }
 #pragma unroll
       for (int w = 0; w < MW; ++w) ncol += __popcll(fm[w] & ~bits_below(last_rd + 1 - 64 * w));
-      if (TB.partial && last_rd >= 0)
-        atomicMax(&H->tile_last_rd, static_cast<unsigned long long>(cv0 + last_rd + 1 - static_cast<int64_t>(J.head)));
-      if (lo < hi && cv0 + hi == static_cast<int64_t>(VL) && test_bit(rm, hi - 1)) H->eof_rd = 1u;
+      if (TB.partial && last_rd >= 0)  // the record ends after its delimiter's W bytes
+        atomicMax(&H->tile_last_rd, static_cast<unsigned long long>(cv0 + last_rd + W - static_cast<int64_t>(J.head)));
+      if (lo < hi && cv0 + hi == static_cast<int64_t>(VL) && test_bit(rm, hi - W)) H->eof_rd = 1u;
     }
     PP_WSPAN(1);
     uint64_t sc_tile;
@@ -1045,30 +1083,39 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       uint64_t val = 0;
       int st;
       const int n_in = static_cast<int>(data_before(e) - data_before(a));
-      if (ended && n_in == e - a) {
+      if (ended && n_in == e - a && W == 1) {
         st = n_in > kNumericMaxLen ? kConvFail : convert_value(type, s_tile + a, n_in, &val);
       } else {
-        uint8_t buf[kNumericMaxLen + 1];
+        uint8_t buf[kNumericMaxLen + 2];
         int m = 0;
         for (int y = a; y < e && m <= kNumericMaxLen; ++y) {
           const int u = y / B, i = y - u * B;
           if ((s_dm[u * MW + (i >> 6)] >> (i & 63)) & 1ull) buf[m++] = s_tile[y];
         }
-        if (!ended && m <= kNumericMaxLen) {
+        if (!ended && m <= kNumericMaxLen) {  // the rest of the field, past the tile
           uint32_t s = tile_send;
-          for (uint64_t g = v1; g < VL; ++g) {
-            const uint8_t b = vbase[g];
-            const uint32_t grp = TB.group_of[b];
+          for (uint64_t g = v1; g + W <= VL; g += W) {
+            const uint32_t unit = W == 2 ? (vbase[g] | (vbase[g + 1] << 8)) : vbase[g];
+            const uint32_t grp = unit <= 0xFFu ? TB.group_of[unit] : TB.catch_all;
             const uint32_t tag = (TB.emit[grp] >> (2 * s)) & 3u;
             s = vget(TB.trans[grp], s);
             if (tag == PP_TAG_DATA) {
-              buf[m++] = b;
+              buf[m++] = vbase[g];
+              if (W == 2) buf[m++] = vbase[g + 1];
               if (m > kNumericMaxLen) break;
             } else if (tag != PP_TAG_CONTROL) {
               break;
             }
             if (s == TB.invalid_state) break;
           }
+        }
+        if (W == 2 && m <= kNumericMaxLen) {  // UTF-16LE text converts when it is ASCII
+          bool ascii = (m & 1) == 0;
+          for (int k = 0; ascii && 2 * k < m; ++k) {
+            ascii = buf[2 * k + 1] == 0 && buf[2 * k] < 0x80;
+            buf[k] = buf[2 * k];
+          }
+          m = ascii ? m / 2 : kNumericMaxLen + 1;
         }
         st = m > kNumericMaxLen ? kConvFail : convert_value(type, buf, m, &val);
       }

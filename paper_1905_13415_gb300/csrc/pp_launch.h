@@ -11,6 +11,7 @@ struct ShapeInfo {
   size_t smem_bytes = 0;
   const void* (*kernel)(int nspec) = nullptr;  // pp_tile_kernel<Shape, NSPEC>
   const void* (*infer_kernel)(int nspec) = nullptr;  // its inference form (default shape only)
+  const void* (*units_kernel)(int nspec) = nullptr;  // its form for UTF-16LE code units (some shapes)
 };
 
 // tile configurations selectable with PP_OPT_TILE_CONFIG

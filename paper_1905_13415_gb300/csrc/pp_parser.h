@@ -16,3 +16,11 @@ struct pp_parser {
   uint32_t first_item = 0;
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
 };
+
+// Internal (not in include/parparaw.h): a parse whose scratch comes from the
+// caller's device block of scratch_cap bytes (PP_E_UNSUPPORTED when too
+// small), or is allocated stream-ordered when scratch_block is null; and the
+// scratch bytes a parse of len bytes into rows_cap rows needs.
+pp_status pp_parse_with_scratch(const pp_parser* P, const uint8_t* input, uint64_t len, const pp_columns* out,
+                                cudaStream_t stream, uint8_t* scratch_block, size_t scratch_cap);
+size_t pp_parse_scratch_bytes(const pp_parser* P, uint64_t len, uint64_t rows_cap);

@@ -49,6 +49,8 @@ struct pp_streamer {
   pp_parse_result* res_host = nullptr;  // their pinned host copies
   cudaStream_t s_h2d = nullptr, s_parse = nullptr, s_d2h = nullptr;
   cudaEvent_t h2d_done[2] = {}, parse_done[2] = {}, d2h_done[2] = {}, carry_done = nullptr;
+  uint8_t* scratch[2] = {nullptr, nullptr};  // each output set's parse scratch, sized with it
+  size_t scratch_cap[2] = {0, 0};
 };
 
 namespace {
@@ -98,6 +100,18 @@ pp_status alloc_outset(pp_streamer* S, int b, uint64_t rows_cap, const uint64_t*
   }
   o.rows_cap = rows_cap;
   o.desc.result = S->res_dev + b;
+  // the parse scratch for a whole buffer into this set (status words, bitmaps)
+  const size_t need = pp_parse_scratch_bytes(&S->parser, S->carry + S->part, rows_cap);
+  if (need > S->scratch_cap[b]) {
+    cudaFree(S->scratch[b]);
+    S->scratch[b] = nullptr;
+    S->scratch_cap[b] = 0;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&S->scratch[b]), need)) != cudaSuccess) {
+      free_outset(o);
+      return map_cuda(e);
+    }
+    S->scratch_cap[b] = need;
+  }
   return PP_OK;
 }
 
@@ -108,7 +122,8 @@ pp_status enqueue_parse(pp_streamer* S, int b, uint64_t start, uint64_t length, 
   local.tab.partial = last ? 0 : 1;
   local.tab.skip_records = first ? S->parser.tab.skip_records : 0;
   local.ev_start = local.ev_stop = nullptr;
-  pp_status st = parparaw_parse(&local, length ? S->buf[b] + start : nullptr, length, &S->out[b].desc, S->s_parse);
+  pp_status st = pp_parse_with_scratch(&local, length ? S->buf[b] + start : nullptr, length, &S->out[b].desc,
+                                       S->s_parse, S->scratch[b], S->scratch_cap[b]);
   if (st != PP_OK) return st;
   cudaError_t e = cudaMemcpyAsync(S->res_host + b, S->res_dev + b, sizeof(pp_parse_result), cudaMemcpyDeviceToHost,
                                   S->s_parse);
@@ -213,6 +228,7 @@ extern "C" void parparaw_stream_destroy(pp_streamer* S) {
   for (int b = 0; b < 2; ++b) {
     free_outset(S->out[b]);
     cudaFree(S->buf[b]);
+    cudaFree(S->scratch[b]);
     if (S->h2d_done[b]) cudaEventDestroy(S->h2d_done[b]);
     if (S->parse_done[b]) cudaEventDestroy(S->parse_done[b]);
     if (S->d2h_done[b]) cudaEventDestroy(S->d2h_done[b]);
@@ -231,6 +247,7 @@ extern "C" pp_status parparaw_stream_create(const pp_parser* parser, uint64_t pa
   if (out == nullptr) return PP_E_ARG;
   *out = nullptr;
   if (parser == nullptr || partition_bytes == 0) return PP_E_ARG;
+  if (parser->tab.unit2 && (partition_bytes % 2 != 0 || carry_bytes % 2 != 0)) return PP_E_ARG;  // whole code units
   pp_streamer* S = new (std::nothrow) pp_streamer();
   if (S == nullptr) return PP_E_NOMEM;
   S->parser = *parser;

@@ -24,7 +24,7 @@ struct Tables {
   uint8_t num_slot[PP_MAX_COLUMNS];    // numeric column -> slot, else 0xFF
   uint8_t num_states, num_groups, num_symbols, catch_all;
   uint8_t start_state, invalid_state, idempotent, num_columns;
-  uint8_t num_str, num_num, partial, pad1;  // partial: more input follows
+  uint8_t num_str, num_num, partial, unit2;  // partial: more input follows; unit2: UTF-16LE code units
   uint32_t accept_mask;
   uint32_t skip_records;  // the first n records leave no row (Sec. 4.3)
 };

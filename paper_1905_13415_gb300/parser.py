@@ -162,9 +162,11 @@ class Parser:
     """A validated DFA + symbol groups + schema (parparaw_create)."""
 
     def __init__(self, fmt: Format, schema, tile_config: int = 0, timeout_ms: int | None = None,
-                 grid_limit: int | None = None, skip_records: int = 0):
+                 grid_limit: int | None = None, skip_records: int = 0, utf16le: bool = False):
         """``skip_records``: the first n records (a header, say) are
-        recognised but leave no row (Sec. 4.3, skipping records)."""
+        recognised but leave no row (Sec. 4.3, skipping records).
+        ``utf16le``: the input is UTF-16LE code units (Sec. 4.2); symbols are
+        the format's bytes as code points U+0000..U+00FF."""
         self._lib = _abi.load()
         self.format = fmt
         self.types = [_abi.TYPE_NAMES[t] if isinstance(t, str) else int(t) for t in schema]
@@ -193,6 +195,8 @@ class Parser:
             self.set_option(_abi.OPT_GRID_LIMIT, grid_limit)
         if skip_records:
             self.set_option(_abi.OPT_SKIP_RECORDS, skip_records)
+        if utf16le:
+            self.set_option(_abi.OPT_UTF16LE, 1)
 
     def set_option(self, option: int, value: int) -> None:
         rc = self._lib.parparaw_set_option(self.handle, option, int(value))

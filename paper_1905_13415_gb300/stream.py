@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import time
 
 import torch
 
@@ -81,9 +82,11 @@ class StreamParser:
         nparts = max(1, (n + self.part - 1) // self.part)
         parts = (_abi.pp_host_partition * nparts)()
         res = _abi.pp_stream_result()
+        t0 = time.perf_counter()
         rc = self._lib.parparaw_stream_parse(self.handle, host.data_ptr() if n else None, n,
                                              arena.buf.data_ptr(), arena.buf.numel(), parts, nparts,
                                              ctypes.byref(res))
+        self.last_call_ms = (time.perf_counter() - t0) * 1e3  # the library call alone
         if rc != _abi.OK:
             raise ParparawError(rc, "parparaw_stream_parse")
         return res, parts
