@@ -64,7 +64,7 @@ def recorded_traffic(workload: str):
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and not line.startswith("#") and parts[0] == workload and parts[1] == src:
-            return {"bytes_per_launch": float(parts[2]), "scaled_from": parts[3]}
+            return {"bytes_per_launch": float(parts[2]), "scaled_from": " ".join(parts[3:])}
     return None
 
 
@@ -193,6 +193,60 @@ def run_reference(args):
     return 0
 
 
+def _bits_of(bm, n: int):
+    import numpy as np
+
+    return np.unpackbits(np.asarray(bm, np.uint8), bitorder="little")[:n]
+
+
+def output_digest_parts(pieces, types) -> list:
+    """Per column, SHA-256 of its logical content over a sequence of row
+    ranges [(rows, columns dict list, row_valid)]: string bytes and field
+    lengths, fixed-width values, validity bits; then row_valid bits."""
+    import numpy as np
+
+    # one hash per stream (values, field lengths, validity) of each column
+    hs = [[hashlib.sha256() for _ in range(3)] for _ in range(len(types))] + [[hashlib.sha256()]]
+    for rows, cols, row_valid in pieces:
+        for c, t in enumerate(types):
+            col = cols[c]
+            if col["values"] is None:
+                continue
+            if col["offsets"] is not None:
+                offs = np.asarray(col["offsets"][: rows + 1], np.int64)
+                hs[c][0].update(np.asarray(col["values"][int(offs[0]): int(offs[-1])], np.uint8).tobytes())
+                hs[c][1].update(np.diff(offs).tobytes())
+            else:
+                hs[c][0].update(np.asarray(col["values"][:rows]).tobytes())
+            hs[c][2].update(_bits_of(col["validity"], rows).tobytes())
+        hs[-1][0].update(_bits_of(row_valid, rows).tobytes())
+    return ["/".join(h.hexdigest()[:16] for h in col) for col in hs]
+
+
+def output_digest_device(out, rows: int) -> list:
+    """output_digest_parts of a device Output (copied to the host)."""
+    h = out.to_host(rows)
+    return output_digest_parts([(rows, h["columns"], h["row_valid"])], out.types)
+
+
+def output_digest_partitions(parts, types) -> list:
+    """output_digest_parts of a streamed parse's host partitions."""
+    pieces = []
+    for x in parts:
+        cols = [{k: (v.numpy() if v is not None else None) for k, v in col.items()} for col in x.columns]
+        pieces.append((x.rows, cols, x.row_valid.numpy()))
+    return output_digest_parts(pieces, types)
+
+
+def roofline_line(algo_bytes: int, kern_ms: float, peak: float, peak_kind: str, traffic=None) -> dict:
+    """HBM roofline of the tile kernel: algorithmic bytes (input read once +
+    the exact output layout) over the kernel's CUDA-event time."""
+    achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "kernel": "pp_tile_kernel",
+            "kernel_ms": round(kern_ms, 4), "algorithmic_bytes": int(algo_bytes), "traffic": traffic}
+
+
 def run_other_configs(args, dev, log):
     """The two other plain-parse configurations: the 1 MB mixed CSV (latency of
     one parse: median of many, inputs resident) and the 1e9-byte trip-record
@@ -213,9 +267,14 @@ def run_other_configs(args, dev, log):
         p = Parser(formats.by_name(synth.DIALECT[wl]), synth.SCHEMAS[wl], tile_config=args.tile_config)
         o, res = p.parse(data, rows_cap=rows + 16)
         assert res.status == 0 and res.rows == rows, (name, res)
+        o = p.allocate(rows + 16, [max(int(b), 1) for b in res.values_bytes_needed], device=dev)
         for _ in range(3):
             p.parse_into(data, o, stream=stream)
-        ms = []
+        ms, kms = [], []
+        ks, kt = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for ev in (ks, kt):
+            ev.record(stream)
+        p.set_kernel_events(ks, kt)
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -223,10 +282,17 @@ def run_other_configs(args, dev, log):
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        med = float(np.median(ms))
+            kms.append(ks.elapsed_time(kt))
+        p.set_kernel_events(None, None)
+        med, kmed = float(np.median(ms)), float(np.median(kms))
+        algo = n + o.output_bytes(rows)
+        peak, peak_kind = measured_peak_gbs()
         out[name] = {"workload": desc, "input_bytes": n, "rows": rows, "ms_median": round(med, 4),
                      "GB/s": round(n / (med * 1e-3) / 1e9, 3), "runs": reps,
-                     "note": "one parse (init, tile, finalize kernels) per run, input resident"}
+                     "note": "one parse (init, tile, finalize kernels) per run, input resident",
+                     "roofline": roofline_line(algo, kmed, peak, peak_kind,
+                                               (recorded_traffic(name) or {}).get("bytes_per_launch")
+                                               if size == WORKLOADS[name][2] else None)}
         log(f"{name}: {n} B in {med:.3f} ms (median of {reps})")
         if name == "trip":  # column-count and type inference over the same input (Sec. 4.3)
             inf = p.infer(data)
@@ -326,18 +392,29 @@ def run_batched(args, dev, log):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = max(3, min(args.steps, 10))
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, z in kev:
+        a.record(stream)
+        z.record(stream)
+    timer = items[0][0]  # the batch's first parser carries the tile-kernel events
     e0.record(stream)
-    for _ in range(steps):
+    for k in range(steps):
+        timer.set_kernel_events(*kev[k])
         b.launch(stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    timer.set_kernel_events(None, None)
     batch_ms = e0.elapsed_time(e1) / steps
+    kern_ms = statistics.mean(a.elapsed_time(z) for a, z in kev)
     b.close()
     bad = 0
+    algo = 0
     for i, (p, d, out) in enumerate(items):
         res = out.result()
         if res.status != 0 or res.rows != int(rows[i]):
             bad += 1
+        algo += int(lens[i]) + out.output_bytes(res.rows)
+    peak, peak_kind = measured_peak_gbs()
     # the plain per-input loop on the same inputs
     for p, d, out in items[:50]:
         p.parse_into(d, out, stream=stream)
@@ -348,23 +425,52 @@ def run_batched(args, dev, log):
     e1.record(stream)
     torch.cuda.synchronize()
     loop_ms = e0.elapsed_time(e1)
+    # What the batch costs beyond its bytes: each format's inputs parsed as
+    # one large input of the same bytes (the plain rate without per-input
+    # tails), and the tiles lost to partial last tiles of small inputs.
+    tile = parsers["mixed"].info().tile_bytes
+    tiles = int(sum((int(x) + tile - 1) // tile for x in lens))
+    whole_ms = 0.0
+    for kind in ("mixed", "log"):
+        nbytes = int(sum(int(lens[i]) for i in range(n) if kinds[i] == kind))
+        big = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        m, r = synth.generate_into(kind, synth.BASE_SEED + 40, nbytes, big.data_ptr(), nbytes)
+        dbig = big[:m].to(dev)
+        p = parsers[kind]
+        o = p.allocate(r + 16, [max(m, 1)] * len(p.types), device=dev)
+        p.parse_into(dbig, o, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            p.parse_into(dbig, o, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        whole_ms += e0.elapsed_time(e1) / 3 * nbytes / max(m, 1)
+        del o, dbig, big
     del items, data
     torch.cuda.empty_cache()
     log(f"batched: {total} B in {batch_ms:.2f} ms, loop {loop_ms:.2f} ms, generator {gen_s:.1f} s")
     return {"value": round(total / (batch_ms * 1e-3) / 1e9, 3), "unit": "GB/s", "inputs": n, "bytes": total,
             "ms_per_step": round(batch_ms, 3), "steps": steps, "launches_per_step": 3,
             "tile_config": best, "autotune_ms": {str(k): round(v, 3) for k, v in tuned.items()},
+            "roofline": roofline_line(algo, kern_ms, peak, peak_kind),
             "plain_loop": {"value": round(total / (loop_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
                            "ms": round(loop_ms, 2), "launches": 3 * n},
             "bad_results": bad,
+            "same_bytes_as_two_large_inputs_ms": round(whole_ms, 3),
+            "batch_over_large_inputs": round(batch_ms / whole_ms, 3) if whole_ms > 0 else None,
+            "tiles": tiles, "tiles_if_concatenated": (total + tile - 1) // tile,
             "workload": "10,000 inputs, log-normal sizes 1 KB..64 MB (~6e9 B), half RFC-4180 CSV, half web logs"}
 
 
 def run_served(args, dev, log):
-    """Config 5: Poisson arrivals at 2,000 req/s; request sizes log-normal
-    (median 64 KB, sigma 2) clipped to 4 KB..256 MB, payloads drawn from a
-    device-resident pool of mixed-CSV / review-CSV / web-log inputs; admission
-    capped by a 40 GB output arena; p50 / p99 latency vs the plain parse."""
+    """Config 5: Poisson arrivals at 2,000 req/s for 60 s; request sizes
+    log-normal (median 64 KB, sigma 2) clipped to 4 KB..256 MB, payloads drawn
+    from a device-resident pool of mixed-CSV / review-CSV / web-log inputs;
+    requests sized from their length only (capacity retries); admission capped
+    by a 40 GB output arena; p50 / p99 latency (arrival to the host seeing the
+    result, and to the device completing it) against the plain per-request
+    parse, then a sweep of higher rates until the plain loop saturates."""
     import numpy as np
     import torch
 
@@ -378,30 +484,71 @@ def run_served(args, dev, log):
     kinds = [("mixed", "review", "log")[i % 3] for i in range(npool)]
     seeds = (synth.BASE_SEED + 5) * 1000 + np.arange(npool, dtype=np.uint64)
     host = torch.empty(int(sizes.sum()), dtype=torch.uint8, pin_memory=True)
-    offs, lens, rows = synth.generate_batch_into(kinds, seeds, sizes, host.data_ptr())
+    offs, lens, _ = synth.generate_batch_into(kinds, seeds, sizes, host.data_ptr())
     data = host.to(dev)
     parsers = {k: Parser(formats.by_name(synth.DIALECT[k]), synth.SCHEMAS[k]) for k in ("mixed", "review", "log")}
-    rate = args.serve_rate
-    nreq = int(rate * args.serve_seconds)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
-    picks = rng.integers(0, npool, nreq)
 
-    def make():
-        reqs = []
-        for j, i in enumerate(picks):
-            p = parsers[kinds[i]]
-            d = data[int(offs[i]): int(offs[i]) + int(lens[i])]
-            reqs.append(Request(j, p, d, max(int(rows[i]), 1), [max(int(lens[i]), 1)] * len(p.types)))
-        return reqs
+    def trace(rate, seconds, seed):
+        r = np.random.default_rng(seed)
+        nreq = int(rate * seconds)
+        return np.cumsum(r.exponential(1.0 / rate, nreq)), r.integers(0, npool, nreq)
 
-    served = run_trace(Server(arena_bytes=40 << 30, streams=4, device=dev), make(), arrivals)
-    plain = run_trace_plain(make(), arrivals, device=dev)
+    def make(picks, keep=()):
+        keep = set(keep)
+        return [Request(j, parsers[kinds[i]], data[int(offs[i]): int(offs[i]) + int(lens[i])], keep=j in keep)
+                for j, i in enumerate(picks)]
+
+    def payload_digest(i):
+        out, res = parsers[kinds[i]].parse(data[int(offs[i]): int(offs[i]) + int(lens[i])])
+        return res.status, output_digest_device(out, res.rows)
+
+    rate, secs = args.serve_rate, args.serve_seconds
+    arrivals, picks = trace(rate, secs, synth.BASE_SEED + 5)
+    check = sorted(rng.choice(len(picks), size=min(200, len(picks)), replace=False).tolist())
+    reqs = make(picks, keep=check)
+    served = run_trace(Server(arena_bytes=40 << 30, streams=4, device=dev), reqs, arrivals)
+    # outputs of a sample of served requests against the plain parse of the same payload
+    want = {}
+    bad = 0
+    for j in check:
+        i = int(picks[j])
+        if i not in want:
+            want[i] = payload_digest(i)
+        r = reqs[j]
+        got = (r.status, output_digest_device(r.out, r.rows))
+        bad += got != want[i]
+        r.out = None
+    served["checked"] = len(check)
+    served["mismatched"] = bad
+    assert bad == 0, "served outputs differ from the plain parse"
+    del reqs
+    plain = run_trace_plain(make(picks), arrivals, device=dev)
     log(f"served: {served}; plain: {plain}")
+    sweep = []
+    for k, sweep_rate in enumerate(args.serve_sweep):
+        arr, pk = trace(sweep_rate, args.sweep_seconds, synth.BASE_SEED + 50 + k)
+        s_res = run_trace(Server(arena_bytes=40 << 30, streams=4, device=dev), make(pk), arr)
+        p_res = run_trace_plain(make(pk), arr, device=dev)
+        offered = float(lens[pk].sum()) / args.sweep_seconds / 1e9
+        sweep.append({"rate_per_s": sweep_rate, "seconds": args.sweep_seconds, "offered_GB/s": round(offered, 4),
+                      "served": s_res, "plain": p_res})
+        log(f"sweep {sweep_rate}/s: served {s_res['gbs']} GB/s p99 {s_res['p99_ms']} ms; "
+            f"plain {p_res['gbs']} GB/s p99 {p_res['p99_ms']} ms")
+        if p_res["wall_s"] > 1.5 * args.sweep_seconds:  # the plain loop no longer keeps up: saturated
+            break
+    del data, host
+    torch.cuda.empty_cache()
     return {"value": served["gbs"], "unit": "GB/s", "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"],
-            "requests": nreq, "seconds": args.serve_seconds, "rate_per_s": rate, "rounds": served["rounds"],
-            "wall_s": served["wall_s"], "plain": plain,
-            "workload": f"Poisson {rate}/s for {args.serve_seconds} s; log-normal sizes 4 KB..256 MB (median 64 KB); "
-                        f"pool of {npool} mixed-CSV / review-CSV / web-log payloads; 40 GB arena"}
+            "p50_device_ms": served["p50_device_ms"], "p99_device_ms": served["p99_device_ms"],
+            "requests": len(picks), "seconds": secs, "rate_per_s": rate, "rounds": served["rounds"],
+            "capacity_retries": served["capacity_retries"], "wall_s": served["wall_s"],
+            "checked": served["checked"], "mismatched": served["mismatched"], "plain": plain, "sweep": sweep,
+            "workload": f"Poisson {rate}/s for {secs} s; log-normal sizes 4 KB..256 MB (median 64 KB); "
+                        f"pool of {npool} mixed-CSV / review-CSV / web-log payloads; 40 GB arena; "
+                        f"requests sized from their length (one row per 16 B, string columns as long as the input), "
+                        f"PP_E_CAPACITY retried with the exact sizes",
+            "latency": "arrival to the host seeing the result (p50_ms, p99_ms) and to the device completing it "
+                       "(p50_device_ms, p99_device_ms); the difference is host dispatch and polling"}
 
 
 def main():
@@ -424,7 +571,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-inputs", type=int, default=10_000)
     ap.add_argument("--batch-bytes", type=int, default=6_000_000_000)
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-sweep", type=float, nargs="*", default=[4000.0, 8000.0, 16000.0, 32000.0, 64000.0])
+    ap.add_argument("--sweep-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-pool", type=int, default=1500)
     args = ap.parse_args()
@@ -508,21 +657,18 @@ def main():
     traffic = recorded_traffic(args.workload)
 
     # ------------------------------------------------- end to end (host)
-    # Through the streaming public API: pinned host input -> device, parse,
-    # columns -> pinned host memory, partitions overlapped (Sec. 4.4).
+    # Through the library's streaming entry (parparaw_stream_parse): pinned
+    # host input -> device, parse, columns -> a pinned host arena, partitions
+    # overlapped on three streams with on-device carry-over (Sec. 4.4).
     e2e = None
     if not args.no_e2e:
-        from paper_1905_13415_gb300.stream import StreamParser
+        from paper_1905_13415_gb300.stream import HostArena, StreamParser
 
+        ref_digest = output_digest_device(out, rows)  # the plain device parse, for the check below
         del out
         torch.cuda.empty_cache()
-        sp = StreamParser(parser, partition_bytes=args.partition_bytes, device=dev,
-                          rows_per_byte=rows / n * 1.25 + 1e-6)  # output buffers sized from the first parse
-
-        from paper_1905_13415_gb300.stream import HostArena
-
-        # pinned host memory for the columns, reused by every step
-        arena = HostArena(int(out_bytes_estimate * 1.1) + (64 << 20))
+        sp = StreamParser(parser, partition_bytes=args.partition_bytes, device=dev)
+        arena = HostArena(int(out_bytes_estimate * 1.1) + (64 << 20))  # reused by every step
 
         def e2e_step():
             parts = sp.parse(host_in, arena)
@@ -536,24 +682,31 @@ def main():
         del parts
         if world > 1:
             torch.distributed.barrier()
-        ksteps = max(2, min(args.steps, 5))
+        ksteps = max(10, min(args.steps, 20))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e2e_step_ms = []
+        e2e_step_ms, call_ms = [], []
         for _ in range(ksteps):
             ts = time.perf_counter()
-            got_rows, parts = e2e_step()  # returns with the stream drained
+            got_rows, parts = e2e_step()  # returns with the library's streams drained
             e2e_step_ms.append((time.perf_counter() - ts) * 1e3)
-            del parts
+            call_ms.append(sp.last_call_ms)
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / ksteps
+        verified = output_digest_partitions(parts, parser.types) == ref_digest  # the last timed step's output
+        assert verified, "streamed output differs from the plain parse"
+        del parts
         (e2e_ms,) = max_over_ranks([e2e_ms], world, dev)
         e2e = {"value": round(whole_job_rate(world, n, e2e_ms), 3), "unit": "GB/s",
                "h2d_bytes_per_step": n, "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
+               "median_ms": round(statistics.median(e2e_step_ms), 3),
+               "median_GB/s": round(n / (statistics.median(e2e_step_ms) * 1e-3) / 1e9, 3),
                "steps": ksteps, "step_ms": [round(x, 2) for x in e2e_step_ms],
-               "api": "StreamParser.parse (partitioned, overlapped, carry-over)",
-               "partition_bytes": args.partition_bytes}
-        del sp
+               "library_call_ms": [round(x, 2) for x in call_ms],
+               "api": "parparaw_stream_parse (C ABI; partitions overlapped, carry-over on the device)",
+               "partition_bytes": args.partition_bytes,
+               "verified": "per-column SHA-256 of the last timed step's output equals the plain device parse's"}
+        sp.close()
 
     # ------------------------------------------------------ CPU baseline
     cpu = None
@@ -590,7 +743,10 @@ def main():
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "kernel": "pp_tile_kernel", "kernel_ms": round(kern_ms, 4),
                          "algorithmic_bytes": algo_bytes,
-                         "traffic": traffic["bytes_per_launch"] if traffic else None},
+                         "traffic": traffic["bytes_per_launch"] if traffic else None,
+                         "traffic_source": (f"ncu DRAM bytes, {traffic['scaled_from']} "
+                                            "(profiles/pp_tile_kernel_traffic.txt)") if traffic else
+                                           "no capture of the current kernel sources"},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
