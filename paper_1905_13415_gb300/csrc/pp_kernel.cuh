@@ -149,6 +149,7 @@ struct SmemHead {
   uint32_t npieces_ok;    // pieces written (a prefix of the queue)
   uint32_t w2_g;         // threads per record of the round's step (2)
   uint32_t piece_next;   // the next long-field piece to copy
+  uint32_t w2_next;      // the next run of step (2) work items
   alignas(16) Piece pieces[kMaxPieces];  // read with 16-byte loads
 #ifdef PP_PHASE_TIMING
   long long ph_cycles[32];  // profiling builds only
@@ -1165,6 +1166,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         }
         H->w2_g = g;
         H->piece_next = 0;
+        H->w2_next = 0;
       }
       {
         const uint32_t per = (nwin + NT - 1) / NT;
@@ -1399,7 +1401,15 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           }
         }
       } else
-      for (uint32_t j = tid; j < nk * G; j += NT) {
+      // work items in runs of 32 taken by whichever warp is free (a warp that
+      // copied long pieces late takes fewer), so the tile's last barrier
+      // waits less; a run keeps a warp's lanes on consecutive records
+      for (uint32_t j0 = 0;;) {
+        if (lane == 0) j0 = atomicAdd(&H->w2_next, 32u);
+        j0 = __shfl_sync(0xffffffffu, j0, 0);
+        if (j0 >= nk * G) break;
+        const uint32_t j = j0 + static_cast<uint32_t>(lane);
+        if (j >= nk * G) continue;
         const uint32_t sub = j / nk, k = ks + (j - sub * nk);
         const uint64_t row = row0 + rr0 + k;
         if (row >= rows_cap) continue;
