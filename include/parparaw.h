@@ -182,7 +182,8 @@ typedef enum pp_option {
                                5 = 128x112; 6 = 128x112 (6 blocks/SM);
                                7 = 128x48; 8 = 256x80; 9 = 256x96;
                                10 = 448x64; 11 = 512x48;
-                               12 = 256x112 (3 blocks/SM) */
+                               12 = 256x112 (3 blocks/SM); 13 = 384x128;
+                               14 = 448x128 */
   PP_OPT_TIMEOUT_MS = 2,    /* bound of every device-side wait (default 2000) */
   PP_OPT_GRID_LIMIT = 3,    /* 0 = one block per tile; n = at most n resident
                                blocks looping over tiles (persistent) */

@@ -19,7 +19,7 @@ PHASE_BUILD = os.path.join(HERE, "_build_phase")
 PHASE_LIB = os.path.join(HERE, "libparparaw_phase.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["pp_host.cu", "pp_rows.cu", "pp_stream.cu"] + [f"pp_tile_{s}.cu" for s in ("tiny", "small", "mid", "wide", "m128", "m128x6", "s128", "mid3", "y96", "t448", "w48", "big3")]
+SOURCES = ["pp_host.cu", "pp_rows.cu", "pp_stream.cu"] + [f"pp_tile_{s}.cu" for s in ("tiny", "small", "mid", "wide", "m128", "m128x6", "s128", "mid3", "y96", "t448", "w48", "big3", "q384", "q448")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -178,6 +178,8 @@ ShapeInfo shape_for(int cfg) {
     case 10: return shape_info_t448();
     case 11: return shape_info_w48();
     case 12: return shape_info_big3();
+    case 13: return shape_info_q384();
+    case 14: return shape_info_q448();
     default: return shape_info_t448();
   }
 }
@@ -502,7 +504,7 @@ extern "C" pp_status parparaw_set_option(pp_parser* P, pp_option option, int64_t
   if (P == nullptr) return PP_E_ARG;
   switch (option) {
     case PP_OPT_TILE_CONFIG:
-      if (value < 0 || value > 12) return PP_E_ARG;
+      if (value < 0 || value > 14) return PP_E_ARG;
       P->tile_config = static_cast<int>(value);
       return PP_OK;
     case PP_OPT_TIMEOUT_MS:

@@ -99,8 +99,16 @@ struct TileShape {
   static constexpr int T = NT * B;         // bytes per tile
   static constexpr int MW = (B + 63) / 64; // 64-bit mask words per chunk
   static constexpr int NW = NT / 32;
-  static_assert(T < 32768, "tile positions are 15-bit field-list entries");
+  static_assert(T < 65536, "tile positions are 16-bit field-list entries");
 };
+
+// A field-list entry: [15:0] the field's end position in the tile (its
+// delimiter, or the tile's end for the open field), [23:16] its column
+// (saturated), [24] the open field (after the tile's last delimiter), [25]
+// the field ends a record.
+constexpr uint32_t kEntPos = 0xFFFFu;
+constexpr uint32_t kEntOpen = 1u << 24;
+constexpr uint32_t kEntRec = 1u << 25;
 
 // A piece of a long string field, copied by whichever warp is free; 16
 // bytes, so that a warp reads it with one shared-memory vector load.
@@ -918,9 +926,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       return e;
     };
 
-    // Field list of one round: entry i describes field f0 + i of the tile,
-    // [15:0) its end position (a delimiter, or PE for the open field),
-    // [15] it ends a record, [23:16] its column (saturated), [24] open field.
+    // Field list of one round: entry i describes field f0 + i of the tile
+    // (the kEnt* layout: end position, column, open field, ends a record).
     // s_rec[k] = first entry of the round's k-th record.  The thread that
     // writes the round's last entry leaves the next round's starting point.
     // The start of a round: the end of its field f0 - 1 (the tile's data start
@@ -959,7 +966,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           const bool rd = test_bit(rm, d);
           if (g >= f0) {
             const int pos = tid * B + d;
-            s_fe[g - f0] = static_cast<uint32_t>(pos) | (rd ? 0x8000u : 0u) | (min(c, 255u) << 16);
+            s_fe[g - f0] = static_cast<uint32_t>(pos) | (rd ? kEntRec : 0u) | (min(c, 255u) << 16);
             if (rd && g + 1 < f1) s_rec[rr + 1 - rr0] = static_cast<uint16_t>(g + 1 - f0);
             if (g + 1 == f1) {
               H->rr_last = rr;
@@ -976,8 +983,8 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         }
       }
       if (tid == NT - 1 && ND >= f0 && ND < f1) {
-        s_fe[ND - f0] = static_cast<uint32_t>(PE) | (trailing ? 0x8000u : 0u) | (min(col_end, 255u) << 16) |
-                        0x1000000u;
+        s_fe[ND - f0] = static_cast<uint32_t>(PE) | (trailing ? kEntRec : 0u) | (min(col_end, 255u) << 16) |
+                        kEntOpen;
         H->rr_last = rec_tile;
       }
       __syncthreads();
@@ -991,10 +998,10 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       const uint32_t b1 = min(tid * per + per, nwin);
       const uint32_t b0 = min(max(tid * per, first_kept(r0.rr0, nwin)), b1);
       for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
-      int eprev = b0 == 0 ? r0.prev_pos : static_cast<int>(s_fe[b0 - 1] & 0x7FFFu);
+      int eprev = b0 == 0 ? r0.prev_pos : static_cast<int>(s_fe[b0 - 1] & kEntPos);
       for (uint32_t g = b0; g < b1; ++g) {  // data bytes are counted for string fields only
         const uint32_t fe = s_fe[g];
-        const int e = static_cast<int>(fe & 0x7FFFu);
+        const int e = static_cast<int>(fe & kEntPos);
         const uint32_t c = (fe >> 16) & 0xFFu;
         if (c < C && TB.str_slot[c] != 0xFF)
           s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(data_before(e) - data_before(eprev + 1));
@@ -1181,7 +1188,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           const uint32_t fe = s_fe[g];
           const uint32_t c = (fe >> 16) & 0xFFu;
           const bool str = NS > 0 && c < C && TB.str_slot[c] != 0xFF;
-          const bool rej = !INFER && (fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead);
+          const bool rej = !INFER && (fe & kEntRec) && c + 1 != C && !((fe & kEntOpen) != 0 && open_dead);
           if (str || rej) work |= 1ull << (g - b0);
         }
         const int trips = __reduce_max_sync(0xffffffffu, static_cast<unsigned>(__popcll(work)));
@@ -1193,9 +1200,9 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           if (work) {
           const uint32_t g = b0 + static_cast<uint32_t>(__ffsll(static_cast<long long>(work)) - 1);
           work &= work - 1;
-          const int eprev = g == 0 ? prev_pos : static_cast<int>(s_fe[g - 1] & 0x7FFFu);
+          const int eprev = g == 0 ? prev_pos : static_cast<int>(s_fe[g - 1] & kEntPos);
           const uint32_t fe = s_fe[g];
-          const int e = static_cast<int>(fe & 0x7FFFu);
+          const int e = static_cast<int>(fe & kEntPos);
           e_cur = e;
           const uint32_t c = (fe >> 16) & 0xFFu;
           if (NS > 0) {
@@ -1205,7 +1212,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
               const uint16_t run = static_cast<uint16_t>(s_cnt[slot * NT + tid] + (de - dprev));
               s_cnt[slot * NT + tid] = run;
               s_fo[g] = static_cast<uint16_t>(run - de);
-              if (de > dprev && !(((fe >> 24) & 1u) && open_dead)) {
+              if (de > dprev && !(((fe & kEntOpen) != 0) && open_dead)) {
                 const uint64_t off = static_cast<uint64_t>(H->col_base[slot]) + static_cast<uint16_t>(run - (de - dprev));
                 const uint64_t cap = cols[c].values_cap;
                 nb = off >= cap ? 0u : static_cast<uint32_t>(min(static_cast<uint64_t>(de - dprev), cap - off));
@@ -1242,7 +1249,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
               }
             }
           }
-          if (!INFER && (fe & 0x8000u) && c + 1 != C && !((fe >> 24) & 1u && open_dead)) {
+          if (!INFER && (fe & kEntRec) && c + 1 != C && !((fe & kEntOpen) != 0 && open_dead)) {
             // the record ends with the wrong number of fields: reject it and
             // give the missing columns their defaults
             uint32_t klo = 0, khi = nrec_win - 1;
@@ -1343,7 +1350,7 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           const uint32_t gb = s_rec[k], ge = k + 1 < nrec_win ? s_rec[k + 1] : nwin;
           if (sub == 0 && ge > gb) {
             const uint32_t fl = s_fe[ge - 1];
-            if ((fl & 0x8000u) && !(((fl >> 24) & 1u) && open_dead)) {
+            if ((fl & kEntRec) && !(((fl & kEntOpen) != 0) && open_dead)) {
               const uint32_t n = min(((fl >> 16) & 0xFFu) + 1u, static_cast<uint32_t>(PP_INFER_MAX_FIELDS));
               atomicMin(&s_inf[PP_MAX_COLUMNS], n);
               atomicMax(&s_inf[PP_MAX_COLUMNS + 1], n);
@@ -1352,11 +1359,11 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           for (uint32_t g = gb + sub; g < ge; g += G) {
             const uint32_t fe = s_fe[g];
             const uint32_t c = (fe >> 16) & 0xFFu;
-            const bool open = (fe >> 24) & 1u;
+            const bool open = (fe & kEntOpen) != 0;
             if (c >= PP_MAX_COLUMNS || (open && open_dead)) break;
             if (!(f0 + g > 0 || t == 0)) continue;  // started in an earlier tile, typed there
-            const int e = static_cast<int>(fe & 0x7FFFu);
-            const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & 0x7FFFu) + 1 : (f0 == 0 ? P0 : prev_pos + 1);
+            const int e = static_cast<int>(fe & kEntPos);
+            const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & kEntPos) + 1 : (f0 == 0 ? P0 : prev_pos + 1);
             const bool ended = !open || last_tile;
             // the field's data bytes (as in convert_field), then the first
             // type of int32, int64, float64 that takes them, else string
@@ -1417,16 +1424,16 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         for (uint32_t g = gb + sub; g < ge; g += G) {
           const uint32_t fe = s_fe[g];
           const uint32_t c = (fe >> 16) & 0xFFu;
-          const bool open = (fe >> 24) & 1u;
+          const bool open = (fe & kEntOpen) != 0;
           if (c >= C || (open && open_dead)) break;
-          const int e = static_cast<int>(fe & 0x7FFFu);
+          const int e = static_cast<int>(fe & kEntPos);
           const uint32_t slot = TB.str_slot[c];
           if (slot != 0xFF) {
-            if (!open || (fe & 0x8000u))
+            if (!open || (fe & kEntRec))
               cols[c].offsets[row + 1] =
                   H->col_base[slot] + static_cast<uint16_t>(s_fo[g] + data_before(e));
           } else if (TB.num_slot[c] != 0xFF && (f0 + g > 0 || t == 0)) {
-            const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & 0x7FFFu) + 1 : (f0 == 0 ? P0 : prev_pos + 1);
+            const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & kEntPos) + 1 : (f0 == 0 ? P0 : prev_pos + 1);
             convert_field(row, c, a, e, !open || last_tile);
           }
         }

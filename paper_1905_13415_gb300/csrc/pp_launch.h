@@ -27,5 +27,7 @@ ShapeInfo shape_info_y96();     // 256 threads x 96 B  = 24 KiB tiles, 3 blocks 
 ShapeInfo shape_info_t448();    // 448 threads x 64 B  = 28 KiB tiles, 2 blocks / SM
 ShapeInfo shape_info_w48();     // 512 threads x 48 B  = 24 KiB tiles, 2 blocks / SM
 ShapeInfo shape_info_big3();    // 256 threads x 112 B = 28 KiB tiles, 3 blocks / SM
+ShapeInfo shape_info_q384();    // 384 threads x 128 B = 48 KiB tiles, 2 blocks / SM
+ShapeInfo shape_info_q448();    // 448 threads x 128 B = 56 KiB tiles, 2 blocks / SM
 
 }  // namespace pp

@@ -21,7 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
-CONFIGS = list(range(1, 13))
+CONFIGS = list(range(1, 15))
 
 
 @pytest.fixture(scope="module")

@@ -15,7 +15,7 @@ from parity import assert_same, oracle_parse
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-CONFIGS = list(range(1, 13))
+CONFIGS = list(range(1, 15))
 
 
 @pytest.fixture(scope="module")
