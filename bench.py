@@ -54,17 +54,19 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def recorded_traffic(workload: str):
+def recorded_traffic(workload: str, tile_config: int):
     """DRAM bytes per launch of the tile kernel from the committed ncu
-    summary, if it was taken on the current kernel sources."""
+    summary, if it was taken on the current kernel sources with the same
+    tile shape."""
     path = os.path.join(ROOT, "profiles", "pp_tile_kernel_traffic.txt")
     if not os.path.exists(path):
         return None
     src = csv_hash_of_sources()
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 4 and not line.startswith("#") and parts[0] == workload and parts[1] == src:
-            return {"bytes_per_launch": float(parts[2]), "scaled_from": " ".join(parts[3:])}
+        if (len(parts) >= 5 and not line.startswith("#") and parts[0] == workload and parts[1] == src
+                and parts[2] == str(tile_config)):
+            return {"bytes_per_launch": float(parts[3]), "scaled_from": " ".join(parts[4:])}
     return None
 
 
@@ -247,6 +249,19 @@ def roofline_line(algo_bytes: int, kern_ms: float, peak: float, peak_kind: str, 
             "kernel_ms": round(kern_ms, 4), "algorithmic_bytes": int(algo_bytes), "traffic": traffic}
 
 
+def pick_tile_shape(args, parser, data, out) -> dict:
+    """The tile shape of a plain-parse line: --tile-config when given, else
+    the autotuner's pick (every candidate shape times a parse of the resident
+    input before the timed region)."""
+    from paper_1905_13415_gb300.autotune import autotune_plain
+
+    if args.tile_config:
+        return {"tile_config": args.tile_config, "tile_shape": "fixed by --tile-config"}
+    best, ms = autotune_plain(parser, data, out, reps=3)
+    return {"tile_config": best, "tile_shape": "autotuned on the resident input",
+            "autotune_ms": {str(k): round(v, 3) for k, v in ms.items()}}
+
+
 def run_other_configs(args, dev, log):
     """The two other plain-parse configurations: the 1 MB mixed CSV (latency of
     one parse: median of many, inputs resident) and the 1e9-byte trip-record
@@ -268,6 +283,7 @@ def run_other_configs(args, dev, log):
         o, res = p.parse(data, rows_cap=rows + 16)
         assert res.status == 0 and res.rows == rows, (name, res)
         o = p.allocate(rows + 16, [max(int(b), 1) for b in res.values_bytes_needed], device=dev)
+        tuned = pick_tile_shape(args, p, data, o)
         for _ in range(3):
             p.parse_into(data, o, stream=stream)
         ms, kms = [], []
@@ -287,11 +303,11 @@ def run_other_configs(args, dev, log):
         med, kmed = float(np.median(ms)), float(np.median(kms))
         algo = n + o.output_bytes(rows)
         peak, peak_kind = measured_peak_gbs()
-        out[name] = {"workload": desc, "input_bytes": n, "rows": rows, "ms_median": round(med, 4),
+        out[name] = {"workload": desc, "input_bytes": n, "rows": rows, **tuned, "ms_median": round(med, 4),
                      "GB/s": round(n / (med * 1e-3) / 1e9, 3), "runs": reps,
                      "note": "one parse (init, tile, finalize kernels) per run, input resident",
                      "roofline": roofline_line(algo, kmed, peak, peak_kind,
-                                               (recorded_traffic(name) or {}).get("bytes_per_launch")
+                                               (recorded_traffic(name, tuned["tile_config"]) or {}).get("bytes_per_launch")
                                                if size == WORKLOADS[name][2] else None)}
         log(f"{name}: {n} B in {med:.3f} ms (median of {reps})")
         if name == "trip":  # column-count and type inference over the same input (Sec. 4.3)
@@ -559,7 +575,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="review", choices=sorted(WORKLOADS))
     ap.add_argument("--size", type=int, default=0, help="input bytes (default: the workload's size)")
-    ap.add_argument("--tile-config", type=int, default=0)
+    ap.add_argument("--tile-config", type=int, default=0, help="tile shape (default: autotuned per workload)")
     ap.add_argument("--cpu-sample", type=int, default=1_500_000_000,
                     help="bytes of the workload the CPU baseline parses")
     ap.add_argument("--ref-sample", type=int, default=256_000_000)
@@ -615,6 +631,7 @@ def main():
     res = out.result()
     assert res.status == 0 and res.rows == gen_rows
     rows = res.rows
+    tuned = pick_tile_shape(args, parser, data, out)
     algo_bytes = n + out.output_bytes(rows)  # input read once + exact output layout
     out_bytes_estimate = out.output_bytes(rows)
 
@@ -654,7 +671,7 @@ def main():
     value = whole_job_rate(world, n, step_ms)
     peak, peak_kind = measured_peak_gbs()
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(args.workload)
+    traffic = recorded_traffic(args.workload, tuned["tile_config"])
 
     # ------------------------------------------------- end to end (host)
     # Through the library's streaming entry (parparaw_stream_parse): pinned
@@ -738,6 +755,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": desc, "input_bytes": n, "rows": rows, "columns": len(schema),
                        "tile_bytes": parser.info().tile_bytes, "parallelism": f"replicas x{world}",
+                       **tuned,
                        "l2": "input larger than L2 (no flush needed)", "generator_s": round(gen_s, 2)},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,

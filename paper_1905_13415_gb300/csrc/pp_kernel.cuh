@@ -990,24 +990,10 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       __syncthreads();
     };
 
-    // Per-slot string bytes of the round's fields; each thread takes an
-    // equal share of consecutive entries.  Leaves the exclusive per-thread
-    // sums in s_cnt and the round totals in round_tot.
-    auto count_round = [&](uint32_t nwin, RoundStart r0) {
-      const uint32_t per = (nwin + NT - 1) / NT;
-      const uint32_t b1 = min(tid * per + per, nwin);
-      const uint32_t b0 = min(max(tid * per, first_kept(r0.rr0, nwin)), b1);
-      for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
-      int eprev = b0 == 0 ? r0.prev_pos : static_cast<int>(s_fe[b0 - 1] & kEntPos);
-      for (uint32_t g = b0; g < b1; ++g) {  // data bytes are counted for string fields only
-        const uint32_t fe = s_fe[g];
-        const int e = static_cast<int>(fe & kEntPos);
-        const uint32_t c = (fe >> 16) & 0xFFu;
-        if (c < C && TB.str_slot[c] != 0xFF)
-          s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(data_before(e) - data_before(eprev + 1));
-        eprev = e;
-      }
-      // block scan of the per-slot counts, two 16-bit slots per word
+    // Block scan of the per-thread, per-slot counts in s_cnt (two 16-bit
+    // slots per word; a slot's total is at most T < 2^16): leaves the
+    // exclusive per-thread sums in s_cnt and the totals in round_tot.
+    auto scan_counts = [&]() {
       const uint32_t K = (NS + 1) / 2;
       uint32_t incl[PP_MAX_STRING_COLUMNS / 2], own[PP_MAX_STRING_COLUMNS / 2];
 #pragma unroll
@@ -1046,6 +1032,67 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       __syncwarp();
     };
 
+    // Per-slot string bytes of the round's fields; each thread takes an
+    // equal share of consecutive entries, then the counts are scanned.
+    auto count_round = [&](uint32_t nwin, RoundStart r0) {
+      const uint32_t per = (nwin + NT - 1) / NT;
+      const uint32_t b1 = min(tid * per + per, nwin);
+      const uint32_t b0 = min(max(tid * per, first_kept(r0.rr0, nwin)), b1);
+      for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
+      int eprev = b0 == 0 ? r0.prev_pos : static_cast<int>(s_fe[b0 - 1] & kEntPos);
+      for (uint32_t g = b0; g < b1; ++g) {  // data bytes are counted for string fields only
+        const uint32_t fe = s_fe[g];
+        const int e = static_cast<int>(fe & kEntPos);
+        const uint32_t c = (fe >> 16) & 0xFFu;
+        if (c < C && TB.str_slot[c] != 0xFF)
+          s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(data_before(e) - data_before(eprev + 1));
+        eprev = e;
+      }
+      scan_counts();
+    };
+
+    // The tile's per-slot string bytes without a field list (for tiles of
+    // several rounds, whose lists are built again when emitted): each thread
+    // splits its chunk at its delimiters and adds each piece's data bytes to
+    // the slot of the field it belongs to -- the field open at the chunk's
+    // start has the column and record the o-scan gave it.  Fields of skipped
+    // records count nothing.  The totals land in round_tot.
+    auto count_chunks = [&]() {
+      for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
+      const uint64_t rec0 = H->prefix_rc & kRecMask;
+      const uint64_t S = TB.skip_records;
+      uint64_t dmk[MW], dl[MW];
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {
+        dmk[w] = s_dm[tid * MW + w];
+        dl[w] = fm[w] | rm[w];
+      }
+      uint32_t c = col_start, rr = row_start, done = 0;
+      auto add = [&](uint32_t upto) {  // data bytes up to here belong to field (rr, c)
+        if (upto > done && c < C && TB.str_slot[c] != 0xFF && rec0 + rr >= S)
+          s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(upto - done);
+        done = upto;
+      };
+      BitIter<MW> it(dl);
+      for (int d = it.next(); d >= 0; d = it.next()) {
+        uint32_t before = 0;
+#pragma unroll
+        for (int w = 0; w < MW; ++w) before += __popcll(dmk[w] & bits_below(d - 64 * w));
+        add(before);
+        if (test_bit(rm, d)) {
+          ++rr;
+          c = 0;
+        } else {
+          c = min(c + 1, kColSat);
+        }
+      }
+      uint32_t all = 0;
+#pragma unroll
+      for (int w = 0; w < MW; ++w) all += __popcll(dmk[w]);
+      add(all);
+      scan_counts();
+    };
+
     auto round_start = [&](uint32_t r) -> RoundStart {  // after next_round's barrier for r > 0
       return r == 0 ? first_round : RoundStart{H->prev_pos, H->rr0};
     };
@@ -1061,14 +1108,14 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
 
     // ------------------------ pass 1: string bytes per column + chain 3
     if (NS > 0) {
-      for (uint32_t r = 0; r < nrounds; ++r) {
-        const uint32_t f0 = r * FCAP, f1 = min(f0 + FCAP, NF);
-        build_round(f0, f1, round_start(r));
+      if (nrounds == 1) {  // the round stays in place for pass 2
+        build_round(0, NF, first_round);
         PP_PHASE(13);
-        count_round(f1 - f0, round_start(r));
-        if (r + 1 < nrounds) next_round();
+        count_round(NF, first_round);
+      } else {
+        count_chunks();
       }
-      if (tid < static_cast<int>(NS)) H->tile_tot[tid] = H->round_base[tid] + H->round_tot[tid];
+      if (tid < static_cast<int>(NS)) H->tile_tot[tid] = H->round_tot[tid];
       __syncwarp();  // written and read by warp 0 (NS <= 32)
       PP_PHASE(6);
       // chain 3: per-slot byte counts, summed over the predecessors; all

@@ -2,8 +2,9 @@
 benchmark times, element by element against the oracle.
 
 - the exact 1e6-byte mixed CSV input of the latency line, compared whole;
-- the 1e9-byte trip-like CSV and the 4.8e9-byte review-like CSV, default tile
-  shape, one plain parse each: every record is compared.  The output is too
+- the 1e9-byte trip-like CSV and the 4.8e9-byte review-like CSV, tile shape
+  picked by the autotuner on the resident input (as the benchmark picks it),
+  one plain parse each: every record is compared.  The output is too
   large for one oracle run, so the oracle parses the input in pieces of whole
   records (record i of a workload depends only on the seed and i, and a piece
   starts in the start state after a record delimiter, so its parse is rows
@@ -80,8 +81,11 @@ def test_full_size_every_record(pp, workload, seed_off, size, piece):
     n, rows = synth.generate_into(workload, seed, size, host.data_ptr(), size)
     data = host[:n].to("cuda")
     del host
-    p = pp.Parser(pp.formats.by_name(dialect), schema)  # the default shape, as benchmarked
+    p = pp.Parser(pp.formats.by_name(dialect), schema)
     out = p.allocate(rows + 16, [n] * len(schema))
+    from paper_1905_13415_gb300.autotune import autotune_plain
+
+    autotune_plain(p, data, out, reps=3)  # the tile shape the benchmark picks the same way
     p.parse_into(data, out)
     torch.cuda.synchronize()
     res = out.result()

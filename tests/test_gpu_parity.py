@@ -6,6 +6,7 @@ Tile configurations 1 (512 B) and 2 (3 KiB) put tile and chunk boundaries
 inside every construct; 0 is the default shape used by the benchmark."""
 from __future__ import annotations
 
+import functools
 import json
 import os
 import random
@@ -89,6 +90,52 @@ def test_generated_workloads(pp, workload, nrows, cfg):
     ref = oracle_parse(synth.DIALECT[workload], schema, raw)
     assert ref.rows == nrows and res.status == O.OK
     assert_same(got, res, ref, what=workload)
+
+
+@functools.lru_cache(maxsize=1)
+def _dense_fields(seed: int, nrec: int) -> bytes:
+    """Records of 1-3 byte fields (more fields per tile than one field-list
+    round holds, in every shape): three string columns among integers,
+    quoted fields with doubled quotes, embedded delimiters and newlines,
+    empty fields, and now and then a record one field short or long."""
+    rng = np.random.default_rng(seed)
+    quoted = [b'"' + bytes([a, b]).replace(b'"', b'""') + b'"' for a in b'a,"\n' for b in b'a,"\n']
+    plain = [bytes([a]) for a in b"abcxyz"] + [bytes([a, b]) for a in b"abc" for b in b"xyz"]
+    nfs = np.where(rng.integers(0, 40, nrec) == 0, rng.choice([5, 7], nrec), 6)
+    kind = rng.integers(0, 10, (nrec, 7))
+    pick = rng.integers(0, 1 << 30, (nrec, 7))
+    out = []
+    for i in range(nrec):
+        f = []
+        for c in range(int(nfs[i])):
+            k, x = int(kind[i, c]), int(pick[i, c])
+            if c in (1, 3, 4):  # string columns
+                f.append(b"" if k == 0 else quoted[x % len(quoted)] if k == 1 else plain[x % len(plain)])
+            else:
+                f.append(b"%d" % (x % 100))
+        out.append(b",".join(f) + b"\n")
+    return b"".join(out)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_multi_round_tiles(pp, cfg):
+    # tiles with several field-list rounds: the per-column string byte totals
+    # taken from the chunk masks must equal what the rounds emit
+    raw = _dense_fields(11, 60_000)
+    schema = ["int32", "string", "int64", "string", "string", "int32"]
+    got, res = run(pp, "csv", schema, raw, cfg)
+    ref = oracle_parse("csv", schema, raw)
+    assert ref.rows == 60_000
+    assert_same(got, res, ref, what=cfg)
+    tile = pp.Parser(pp.formats.by_name("csv"), schema, tile_config=cfg).info().tile_bytes
+    # more fields per tile than a round holds (at most T/4 and 4960 entries)
+    assert raw.count(b",") / (len(raw) / tile) > min(tile / 4, 4960)
+    for skip in (3, 20_001):
+        p = pp.Parser(pp.formats.by_name("csv"), schema, tile_config=cfg, skip_records=skip)
+        out, res = p.parse(to_dev(raw))
+        torch.cuda.synchronize()
+        assert_same(out.to_host(min(res.rows, out.rows_cap)), res, oracle_parse("csv", schema, raw, skip),
+                    what=(cfg, skip))
 
 
 @pytest.mark.parametrize("offset", [1, 3, 7, 15])
