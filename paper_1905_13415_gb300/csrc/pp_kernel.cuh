@@ -382,31 +382,6 @@ __device__ __forceinline__ bool test_bit(const uint64_t (&m)[MW], int p) {
   return r;
 }
 
-// Ascending iteration over the set bits of a chunk mask without unrolling the
-// loop body per mask word: the words shift down as they are exhausted.
-template <int MW>
-struct BitIter {
-  uint64_t w[MW];
-  int base;
-  __device__ __forceinline__ explicit BitIter(const uint64_t (&m)[MW]) : base(0) {
-#pragma unroll
-    for (int i = 0; i < MW; ++i) w[i] = m[i];
-  }
-  // next set position, or -1
-  __device__ __forceinline__ int next() {
-    while (w[0] == 0) {
-      if (base + 64 >= 64 * MW) return -1;
-#pragma unroll
-      for (int i = 0; i + 1 < MW; ++i) w[i] = w[i + 1];
-      w[MW - 1] = 0;
-      base += 64;
-    }
-    const int p = base + __ffsll(static_cast<long long>(w[0])) - 1;
-    w[0] &= w[0] - 1;
-    return p;
-  }
-};
-
 // shared -> shared or global byte copy: bytes up to a 4-byte aligned destination, then
 // 32-bit words assembled with funnel shifts, four per step (the source loads
 // of a step are independent).  May read up to 20 bytes past the source end.
@@ -723,12 +698,15 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
     uint64_t vec = kIdentityVec;
     {
       int prev = -W;
-      BitIter<MW> it(spec);
-      for (int p = it.next(); p >= 0; p = it.next()) {
-        const bool run = max(prev + W, lo) < p;
-        const uint32_t g = group_at(p);
-        vec = vcompose(vec, run ? TB.trans_run[g] : TB.trans[g]);
-        prev = p;
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {  // the symbols in order, one mask word at a time
+        for (uint64_t sw = spec[w]; sw; sw &= sw - 1) {
+          const int p = 64 * w + __ffsll(static_cast<long long>(sw)) - 1;
+          const bool run = max(prev + W, lo) < p;
+          const uint32_t g = group_at(p);
+          vec = vcompose(vec, run ? TB.trans_run[g] : TB.trans[g]);
+          prev = p;
+        }
       }
       if (max(prev + W, lo) < hi) vec = vcompose(vec, TB.trans[TB.catch_all]);
     }
@@ -782,30 +760,40 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         }
         s = s1;
       };
-      BitIter<MW> it(spec);
-      for (int p = it.next(); p >= 0; p = it.next()) {
-        const int rs = max(prev + W, lo);
-        const uint32_t g = group_at(p);
-        // one lookup for the catch-all run before the symbol (if any) and the
-        // symbol itself; runs that are not all data take the byte-exact path
-        uint32_t st = TB.step[rs < p ? 1 : 0][g][s];
-        if (st & kStepSlow) {
-          run(rs, p);
-          st = TB.step[0][g][s];
-        }
-        const uint32_t tag = (st >> 3) & 3u;
-        if ((st & kStepInv) && inv_pos < 0) inv_pos = p;
-        // a special symbol is never data unless its tag says so; delimiters
-        // are marked at their first byte
 #pragma unroll
-        for (int w = 0; w < MW; ++w) {
-          const uint64_t bit = (p >> 6) == w ? (1ull << (p & 63)) : 0ull;
-          if (tag == PP_TAG_DATA) dm[w] |= bit | (W == 2 ? bit << 1 : 0ull);
-          else if (tag == PP_TAG_FIELD) fm[w] |= bit;
-          else if (tag == PP_TAG_RECORD) rm[w] |= bit;
+      for (int w = 0; w < MW; ++w) {  // the symbols in order, one mask word at a time
+        // this word's symbols that are data, field and record delimiters
+        // (or-ed in after the word: run() touches only bits before the
+        // current symbol, never an earlier symbol's)
+        uint64_t dw = 0, fw = 0, rw = 0;
+        for (uint64_t sw = spec[w]; sw; sw &= sw - 1) {
+          const int b = __ffsll(static_cast<long long>(sw)) - 1;
+          const int p = 64 * w + b;
+          const int rs = max(prev + W, lo);
+          const uint32_t g = group_at(p);
+          // one lookup for the catch-all run before the symbol (if any) and
+          // the symbol itself; runs that are not all data take the
+          // byte-exact path
+          uint32_t st = TB.step[rs < p ? 1 : 0][g][s];
+          if (st & kStepSlow) {
+            run(rs, p);
+            st = TB.step[0][g][s];
+          }
+          const uint32_t tag = (st >> 3) & 3u;
+          if ((st & kStepInv) && inv_pos < 0) inv_pos = p;
+          // a special symbol is never data unless its tag says so;
+          // delimiters are marked at their first byte (a UTF-16 unit starts
+          // at an even position, so its second byte is in the same word)
+          const uint64_t bit = 1ull << b;
+          if (tag == PP_TAG_DATA) dw |= bit | (W == 2 ? bit << 1 : 0ull);
+          else if (tag == PP_TAG_FIELD) fw |= bit;
+          else if (tag == PP_TAG_RECORD) rw |= bit;
+          s = st & 7u;
+          prev = p;
         }
-        s = st & 7u;
-        prev = p;
+        dm[w] |= dw;
+        fm[w] |= fw;
+        rm[w] |= rw;
       }
       {
         const int rs = max(prev + W, lo);
@@ -958,27 +946,27 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       if (tid == 0) s_rec[0] = 0;
       if (dl_ex < f1 && dl_ex + ndl > f0) {
         uint32_t g = dl_ex, c = col_start, rr = row_start;
-        uint64_t dl[MW];
 #pragma unroll
-        for (int w = 0; w < MW; ++w) dl[w] = fm[w] | rm[w];
-        BitIter<MW> it(dl);
-        for (int d = it.next(); d >= 0 && g < f1; d = it.next(), ++g) {
-          const bool rd = test_bit(rm, d);
-          if (g >= f0) {
-            const int pos = tid * B + d;
-            s_fe[g - f0] = static_cast<uint32_t>(pos) | (rd ? kEntRec : 0u) | (min(c, 255u) << 16);
-            if (rd && g + 1 < f1) s_rec[rr + 1 - rr0] = static_cast<uint16_t>(g + 1 - f0);
-            if (g + 1 == f1) {
-              H->rr_last = rr;
-              H->rr_next = rr + (rd ? 1u : 0u);
-              H->next_prev_pos = pos;
+        for (int w = 0; w < MW; ++w) {  // the delimiters in order, one mask word at a time
+          for (uint64_t dw = fm[w] | rm[w]; dw && g < f1; dw &= dw - 1, ++g) {
+            const int b = __ffsll(static_cast<long long>(dw)) - 1;
+            const bool rd = (rm[w] >> b) & 1ull;
+            if (g >= f0) {
+              const int pos = tid * B + 64 * w + b;
+              s_fe[g - f0] = static_cast<uint32_t>(pos) | (rd ? kEntRec : 0u) | (min(c, 255u) << 16);
+              if (rd && g + 1 < f1) s_rec[rr + 1 - rr0] = static_cast<uint16_t>(g + 1 - f0);
+              if (g + 1 == f1) {
+                H->rr_last = rr;
+                H->rr_next = rr + (rd ? 1u : 0u);
+                H->next_prev_pos = pos;
+              }
             }
-          }
-          if (rd) {
-            ++rr;
-            c = 0;
-          } else {
-            c = min(c + 1, kColSat);
+            if (rd) {
+              ++rr;
+              c = 0;
+            } else {
+              c = min(c + 1, kColSat);
+            }
           }
         }
       }
@@ -1061,35 +1049,28 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       for (uint32_t k = 0; k < NS; ++k) s_cnt[k * NT + tid] = 0;
       const uint64_t rec0 = H->prefix_rc & kRecMask;
       const uint64_t S = TB.skip_records;
-      uint64_t dmk[MW], dl[MW];
-#pragma unroll
-      for (int w = 0; w < MW; ++w) {
-        dmk[w] = s_dm[tid * MW + w];
-        dl[w] = fm[w] | rm[w];
-      }
-      uint32_t c = col_start, rr = row_start, done = 0;
+      uint32_t c = col_start, rr = row_start, done = 0, base = 0;
       auto add = [&](uint32_t upto) {  // data bytes up to here belong to field (rr, c)
         if (upto > done && c < C && TB.str_slot[c] != 0xFF && rec0 + rr >= S)
           s_cnt[TB.str_slot[c] * NT + tid] += static_cast<uint16_t>(upto - done);
         done = upto;
       };
-      BitIter<MW> it(dl);
-      for (int d = it.next(); d >= 0; d = it.next()) {
-        uint32_t before = 0;
 #pragma unroll
-        for (int w = 0; w < MW; ++w) before += __popcll(dmk[w] & bits_below(d - 64 * w));
-        add(before);
-        if (test_bit(rm, d)) {
-          ++rr;
-          c = 0;
-        } else {
-          c = min(c + 1, kColSat);
+      for (int w = 0; w < MW; ++w) {  // the delimiters in order, one mask word at a time
+        const uint64_t dmw = s_dm[tid * MW + w];
+        for (uint64_t dw = fm[w] | rm[w]; dw; dw &= dw - 1) {
+          const int b = __ffsll(static_cast<long long>(dw)) - 1;
+          add(base + __popcll(dmw & bits_below(b)));
+          if ((rm[w] >> b) & 1ull) {
+            ++rr;
+            c = 0;
+          } else {
+            c = min(c + 1, kColSat);
+          }
         }
+        base += __popcll(dmw);
       }
-      uint32_t all = 0;
-#pragma unroll
-      for (int w = 0; w < MW; ++w) all += __popcll(dmk[w]);
-      add(all);
+      add(base);
       scan_counts();
     };
 
@@ -1355,11 +1336,12 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       // block waits for it)
       {
         const uint32_t total = H->npieces_ok;
-        for (;;) {
-          uint32_t p = 0;
-          if (lane == 0) p = atomicAdd(&H->piece_next, 1u);
-          p = __shfl_sync(0xffffffffu, p, 0);
-          if (p >= total) break;
+        uint32_t pn = 0;
+        if (lane == 0) pn = atomicAdd(&H->piece_next, 1u);
+        for (uint32_t p = __shfl_sync(0xffffffffu, pn, 0); p < total; p = __shfl_sync(0xffffffffu, pn, 0)) {
+          // the next claim is issued before this piece is copied, so its
+          // latency is hidden behind the copy
+          if (lane == 0) pn = atomicAdd(&H->piece_next, 1u);
           const uint4 raw = reinterpret_cast<const uint4*>(H->pieces)[p];
           uint8_t* dst = reinterpret_cast<uint8_t*>((static_cast<uint64_t>(raw.y) << 32) | raw.x);
           const int x0 = static_cast<int>(raw.z & 0xFFFFu), len = static_cast<int>(raw.z >> 16);
@@ -1458,10 +1440,9 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
       // work items in runs of 32 taken by whichever warp is free (a warp that
       // copied long pieces late takes fewer), so the tile's last barrier
       // waits less; a run keeps a warp's lanes on consecutive records
-      for (uint32_t j0 = 0;;) {
-        if (lane == 0) j0 = atomicAdd(&H->w2_next, 32u);
-        j0 = __shfl_sync(0xffffffffu, j0, 0);
-        if (j0 >= nk * G) break;
+      for (uint32_t jn = lane == 0 ? atomicAdd(&H->w2_next, 32u) : 0u, j0 = __shfl_sync(0xffffffffu, jn, 0);
+           j0 < nk * G; j0 = __shfl_sync(0xffffffffu, jn, 0)) {
+        if (lane == 0) jn = atomicAdd(&H->w2_next, 32u);  // the next run's claim, ahead of this one's work
         const uint32_t j = j0 + static_cast<uint32_t>(lane);
         if (j >= nk * G) continue;
         const uint32_t sub = j / nk, k = ks + (j - sub * nk);
