@@ -881,14 +881,24 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
 
     // Data bytes of the tile before tile position p (p in [0, T]).
     auto data_before = [&](int p) -> uint32_t {
-      const int u = p / B;
-      const int off = p - u * B;
-      uint32_t n = s_dex[u];
-      if (off > 0) {
+      if constexpr (B % 64 == 0) {  // whole mask words per chunk: word p / 64 of the tile holds p
+        const int wi = p >> 6, u = wi / MW, w = wi - u * MW;
+        uint32_t n = s_dex[u];
 #pragma unroll
-        for (int w = 0; w < MW; ++w) n += __popcll(s_dm[u * MW + w] & bits_below(off - 64 * w));
+        for (int k = 0; k + 1 < MW; ++k)
+          if (k < w) n += __popcll(s_dm[u * MW + k]);
+        if (p & 63) n += __popcll(s_dm[wi] & ((1ull << (p & 63)) - 1ull));
+        return n;
+      } else {
+        const int u = p / B;
+        const int off = p - u * B;
+        uint32_t n = s_dex[u];
+        if (off > 0) {
+#pragma unroll
+          for (int w = 0; w < MW; ++w) n += __popcll(s_dm[u * MW + w] & bits_below(off - 64 * w));
+        }
+        return n;
       }
-      return n;
     };
 
     // First data position in [p, e), else e.  Mask bits at or past B are
@@ -899,17 +909,6 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
         const uint64_t w = s_dm[u * MW + (i >> 6)] & ~bits_below(i & 63);
         if (w) return min(u * B + (i & ~63) + __ffsll(static_cast<long long>(w)) - 1, e);
         p = (i & ~63) + 64 >= B ? (u + 1) * B : u * B + (i & ~63) + 64;
-      }
-      return e;
-    };
-
-    // First non-data position in [p, e), else e.
-    auto first_gap = [&](int p, int e) -> int {
-      while (p < e) {
-        const int u = p / B, i = p - u * B, wi = i >> 6;
-        const uint64_t w = ~s_dm[u * MW + wi] & bits_below(B - 64 * wi) & ~bits_below(i & 63);
-        if (w) return min(u * B + 64 * wi + __ffsll(static_cast<long long>(w)) - 1, e);
-        p = 64 * wi + 64 >= B ? (u + 1) * B : u * B + 64 * wi + 64;
       }
       return e;
     };
@@ -1348,16 +1347,36 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
           const uint32_t fd = raw.w & 0xFFFFu, nb = raw.w >> 16;
           if (fd == kContiguousPiece) {
             warp_copy_out(dst, s_tile + x0, len, lane);
-          } else {  // data bytes with gaps (a doubled quote, say): its runs of data bytes one by one
-            const uint32_t d0 = data_before(static_cast<int>(fd));
+          } else {
+            // data bytes with gaps (a doubled quote, say): the runs between
+            // the piece's non-data bytes, in order.  Each lane reads the
+            // data bits of 16 aligned positions (inside one mask word of one
+            // chunk); the warp walks the non-data positions it found.
             const int x1 = x0 + len;
-            for (int a = first_data(x0, x1); a < x1;) {
-              const int z = first_gap(a, x1);
-              const uint32_t rank = data_before(a) - d0;
-              if (rank >= nb) break;
-              warp_copy_out(dst + rank, s_tile + a, min(z - a, static_cast<int>(nb - rank)), lane);
-              a = first_data(z, x1);
+            uint32_t rank = data_before(x0) - data_before(static_cast<int>(fd));  // of run start a
+            int a = x0;
+            for (int q0 = x0 & ~15; q0 < x1 && rank < nb; q0 += 512) {
+              const int q = q0 + 16 * lane;
+              uint32_t gap = 0;
+              if (q < x1) {
+                const int u = q / B, i = q - u * B;
+                gap = ~static_cast<uint32_t>(s_dm[u * MW + (i >> 6)] >> (i & 63)) & 0xFFFFu;
+                if (q < x0) gap &= ~((1u << (x0 - q)) - 1u);
+                if (x1 - q < 16) gap &= (1u << (x1 - q)) - 1u;
+              }
+              for (uint32_t ls = __ballot_sync(0xffffffffu, gap != 0); ls && rank < nb; ls &= ls - 1) {
+                const int src = __ffs(static_cast<int>(ls)) - 1;
+                for (uint32_t gm = __shfl_sync(0xffffffffu, gap, src); gm && rank < nb; gm &= gm - 1) {
+                  const int g = q0 + 16 * src + __ffs(static_cast<int>(gm)) - 1;
+                  if (g > a) {
+                    warp_copy_out(dst + rank, s_tile + a, min(g - a, static_cast<int>(nb - rank)), lane);
+                    rank += static_cast<uint32_t>(g - a);
+                  }
+                  a = g + 1;
+                }
+              }
             }
+            if (a < x1 && rank < nb) warp_copy_out(dst + rank, s_tile + a, min(x1 - a, static_cast<int>(nb - rank)), lane);
           }
         }
       }

@@ -138,6 +138,47 @@ def test_multi_round_tiles(pp, cfg):
                     what=(cfg, skip))
 
 
+def _gapped_long_fields(seed: int, nrec: int) -> bytes:
+    """Quoted fields of 30-3,000 bytes with doubled quotes (non-data bytes
+    inside the field) at random places, in runs, and next to multiples of
+    16 and 512 bytes of the field (where long fields are cut into pieces)."""
+    rng = np.random.default_rng(seed)
+    alphabet = np.frombuffer(b"abcdefgh ,\n", dtype=np.uint8)
+    recs = []
+    for i in range(nrec):
+        n = int(rng.integers(30, 3000))
+        body = rng.choice(alphabet, n).tobytes()
+        pos = {int(x) for x in rng.integers(0, n, int(rng.integers(0, 6)))}
+        if i % 3 == 0:
+            pos.add(min(n, max(0, 512 * int(rng.integers(0, n // 512 + 1)) + int(rng.integers(-3, 4)))))
+        if i % 5 == 0:
+            pos.add(min(n, 16 * int(rng.integers(0, n // 16 + 1))))
+        text, last = [], 0
+        for q in sorted(pos):
+            text += [body[last:q], b'""' * int(rng.integers(1, 4))]
+            last = q
+        text.append(body[last:])
+        recs.append(b'%d,"%s",x%d\n' % (i, b"".join(text), i))
+    return b"".join(recs)
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3, 10, 13])
+def test_long_fields_with_gaps(pp, cfg):
+    # the long-field pieces that hold non-data bytes are copied run by run
+    raw = _gapped_long_fields(cfg, 2500)
+    schema = ["int32", "string", "string"]
+    ref = oracle_parse("csv", schema, raw)
+    assert ref.status == O.OK and ref.rows == 2500
+    got, res = run(pp, "csv", schema, raw, cfg)
+    assert_same(got, res, ref, what=cfg)
+    # too few value bytes for the long column: the bytes that fit are the oracle's
+    cap = ref.columns[1].bytes_total // 2 + 7
+    got, res = run(pp, "csv", schema, raw, cfg, rows_cap=ref.rows, caps=[len(raw), cap, len(raw)])
+    assert res.status == -6 and res.values_bytes_needed[1] == ref.columns[1].bytes_total
+    assert np.array_equal(got["columns"][1]["values"][:cap], ref.columns[1].values[:cap])
+    assert np.array_equal(got["columns"][1]["offsets"][: ref.rows + 1], ref.columns[1].offsets[: ref.rows + 1])
+
+
 @pytest.mark.parametrize("offset", [1, 3, 7, 15])
 def test_unaligned_input(pp, offset):
     raw, _ = synth.records("mixed", 5, 0, 500)
