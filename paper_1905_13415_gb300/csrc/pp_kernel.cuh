@@ -179,12 +179,12 @@ struct SmemLayout {
   static constexpr size_t kFe = kDex + ((sizeof(uint16_t) * (Shape::NT + 1) + 15) & ~size_t(15));
   // Field-list capacity: what an SM's shared memory (228 KB, 1 KB reserved
   // per block) leaves at the shape's residency (at least 2 blocks), within
-  // [T/16, T/4] and at most 4960 entries of 8 bytes.  Tiles with more fields
+  // [T/32, T/4] and at most 4960 entries of 8 bytes.  Tiles with more fields
   // are processed in rounds.
   static constexpr int kBlocks = Shape::MINB > 2 ? Shape::MINB : 2;
   static constexpr long kPerBlock = 233472 / kBlocks - 1024;
   static constexpr long kFit = (kPerBlock - static_cast<long>(kFe)) / 8;
-  static constexpr long kLo = kFit > Shape::T / 16 ? kFit : Shape::T / 16;
+  static constexpr long kLo = kFit > Shape::T / 32 ? kFit : Shape::T / 32;
   static constexpr long kHi = Shape::T / 4 < 4960 ? Shape::T / 4 : 4960;
   static constexpr int kFcap = static_cast<int>(((kLo < kHi ? kLo : kHi) & ~31L) < 64 ? 64 : ((kLo < kHi ? kLo : kHi) & ~31L));
   static constexpr size_t kFo = kFe + sizeof(uint32_t) * kFcap;
