@@ -334,6 +334,10 @@ typedef struct pp_host_partition {
   uint64_t input_bytes;  /* bytes parsed for it */
   pp_column cols[PP_MAX_COLUMNS];
   uint8_t* row_valid;
+  /* device time (CUDA events on the streamer's streams, milliseconds) of the
+   * partition's copy in, its parse (the launches and the result read-back)
+   * and the copy out of its columns; each excludes the waits before it */
+  float h2d_ms, parse_ms, d2h_ms;
 } pp_host_partition;
 
 /* Outcome of a streamed parse.

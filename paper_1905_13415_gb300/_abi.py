@@ -81,7 +81,8 @@ RESULT_BYTES = ctypes.sizeof(pp_parse_result)
 
 class pp_host_partition(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int64), ("row0", ctypes.c_int64), ("input_offset", ctypes.c_uint64),
-                ("input_bytes", ctypes.c_uint64), ("cols", pp_column * MAX_COLUMNS), ("row_valid", ctypes.c_void_p)]
+                ("input_bytes", ctypes.c_uint64), ("cols", pp_column * MAX_COLUMNS), ("row_valid", ctypes.c_void_p),
+                ("h2d_ms", ctypes.c_float), ("parse_ms", ctypes.c_float), ("d2h_ms", ctypes.c_float)]
 
 
 class pp_stream_result(ctypes.Structure):

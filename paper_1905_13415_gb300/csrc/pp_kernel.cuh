@@ -659,26 +659,28 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
             }
           }
         }
-      } else
+      } else {
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const uint4 q = src[v];
-        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+        for (int v = 0; v < VPT; ++v) {
+          const uint4 q = src[v];
+          const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          // zero-byte test of the word against every symbol; a flagged byte
-          // that is not a symbol (borrow from a zero byte below) is harmless:
-          // it is simulated on its own with the catch-all transition
-          uint32_t acc = 0;
+          for (int k = 0; k < 4; ++k) {
+            // zero-byte test of the word against every symbol; a flagged
+            // byte that is not a symbol (borrow from a zero byte below) is
+            // harmless: it is simulated on its own with the catch-all
+            // transition
+            uint32_t acc = 0;
 #pragma unroll
-          for (int s = 0; s < NSPEC; ++s) {
-            const uint32_t x = wd[k] ^ rep[s];
-            acc |= (x - 0x01010101u) & ~x;
+            for (int s = 0; s < NSPEC; ++s) {
+              const uint32_t x = wd[k] ^ rep[s];
+              acc |= (x - 0x01010101u) & ~x;
+            }
+            acc &= 0x80808080u;
+            const uint32_t bits4 = (((acc >> 7) * 0x00204081u) >> 21) & 0xFu;
+            const int pos = 16 * v + 4 * k;
+            spec[pos >> 6] |= static_cast<uint64_t>(bits4) << (pos & 63);
           }
-          acc &= 0x80808080u;
-          const uint32_t bits4 = (((acc >> 7) * 0x00204081u) >> 21) & 0xFu;
-          const int pos = 16 * v + 4 * k;
-          spec[pos >> 6] |= static_cast<uint64_t>(bits4) << (pos & 63);
         }
       }
 #pragma unroll
@@ -1455,33 +1457,35 @@ __global__ void __launch_bounds__(Shape::NT, Shape::MINB) pp_tile_kernel(const _
             atomicMax(&s_inf[c], rank);
           }
         }
-      } else
-      // work items in runs of 32 taken by whichever warp is free (a warp that
-      // copied long pieces late takes fewer), so the tile's last barrier
-      // waits less; a run keeps a warp's lanes on consecutive records
-      for (uint32_t jn = lane == 0 ? atomicAdd(&H->w2_next, 32u) : 0u, j0 = __shfl_sync(0xffffffffu, jn, 0);
-           j0 < nk * G; j0 = __shfl_sync(0xffffffffu, jn, 0)) {
-        if (lane == 0) jn = atomicAdd(&H->w2_next, 32u);  // the next run's claim, ahead of this one's work
-        const uint32_t j = j0 + static_cast<uint32_t>(lane);
-        if (j >= nk * G) continue;
-        const uint32_t sub = j / nk, k = ks + (j - sub * nk);
-        const uint64_t row = row0 + rr0 + k;
-        if (row >= rows_cap) continue;
-        const uint32_t gb = s_rec[k], ge = k + 1 < nrec_win ? s_rec[k + 1] : nwin;
-        for (uint32_t g = gb + sub; g < ge; g += G) {
-          const uint32_t fe = s_fe[g];
-          const uint32_t c = (fe >> 16) & 0xFFu;
-          const bool open = (fe & kEntOpen) != 0;
-          if (c >= C || (open && open_dead)) break;
-          const int e = static_cast<int>(fe & kEntPos);
-          const uint32_t slot = TB.str_slot[c];
-          if (slot != 0xFF) {
-            if (!open || (fe & kEntRec))
-              cols[c].offsets[row + 1] =
-                  H->col_base[slot] + static_cast<uint16_t>(s_fo[g] + data_before(e));
-          } else if (TB.num_slot[c] != 0xFF && (f0 + g > 0 || t == 0)) {
-            const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & kEntPos) + 1 : (f0 == 0 ? P0 : prev_pos + 1);
-            convert_field(row, c, a, e, !open || last_tile);
+      } else {
+        // work items in runs of 32 taken by whichever warp is free (a warp
+        // that copied long pieces late takes fewer), so the tile's last
+        // barrier waits less; a run keeps a warp's lanes on consecutive
+        // records
+        for (uint32_t jn = lane == 0 ? atomicAdd(&H->w2_next, 32u) : 0u, j0 = __shfl_sync(0xffffffffu, jn, 0);
+             j0 < nk * G; j0 = __shfl_sync(0xffffffffu, jn, 0)) {
+          if (lane == 0) jn = atomicAdd(&H->w2_next, 32u);  // the next run's claim, ahead of this one's work
+          const uint32_t j = j0 + static_cast<uint32_t>(lane);
+          if (j >= nk * G) continue;
+          const uint32_t sub = j / nk, k = ks + (j - sub * nk);
+          const uint64_t row = row0 + rr0 + k;
+          if (row >= rows_cap) continue;
+          const uint32_t gb = s_rec[k], ge = k + 1 < nrec_win ? s_rec[k + 1] : nwin;
+          for (uint32_t g = gb + sub; g < ge; g += G) {
+            const uint32_t fe = s_fe[g];
+            const uint32_t c = (fe >> 16) & 0xFFu;
+            const bool open = (fe & kEntOpen) != 0;
+            if (c >= C || (open && open_dead)) break;
+            const int e = static_cast<int>(fe & kEntPos);
+            const uint32_t slot = TB.str_slot[c];
+            if (slot != 0xFF) {
+              if (!open || (fe & kEntRec))
+                cols[c].offsets[row + 1] =
+                    H->col_base[slot] + static_cast<uint16_t>(s_fo[g] + data_before(e));
+            } else if (TB.num_slot[c] != 0xFF && (f0 + g > 0 || t == 0)) {
+              const int a = g > 0 ? static_cast<int>(s_fe[g - 1] & kEntPos) + 1 : (f0 == 0 ? P0 : prev_pos + 1);
+              convert_field(row, c, a, e, !open || last_tile);
+            }
           }
         }
       }

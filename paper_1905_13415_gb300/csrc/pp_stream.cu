@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 
 #include "pp_parser.h"
@@ -49,6 +50,9 @@ struct pp_streamer {
   pp_parse_result* res_host = nullptr;  // their pinned host copies
   cudaStream_t s_h2d = nullptr, s_parse = nullptr, s_d2h = nullptr;
   cudaEvent_t h2d_done[2] = {}, parse_done[2] = {}, d2h_done[2] = {}, carry_done = nullptr;
+  // the starts of each set's copy in, parse and copy out (timed against the
+  // *_done events above, for the partitions' device times)
+  cudaEvent_t h2d_start[2] = {}, parse_start[2] = {}, d2h_start[2] = {};
   uint8_t* scratch[2] = {nullptr, nullptr};  // each output set's parse scratch, sized with it
   size_t scratch_cap[2] = {0, 0};
 };
@@ -118,6 +122,8 @@ pp_status alloc_outset(pp_streamer* S, int b, uint64_t rows_cap, const uint64_t*
 // Parses buf[b][start, start + length) into output set b on s_parse, copies
 // its result to pinned host memory and marks the set's parse as done.
 pp_status enqueue_parse(pp_streamer* S, int b, uint64_t start, uint64_t length, bool last, bool first) {
+  cudaError_t e0 = cudaEventRecord(S->parse_start[b], S->s_parse);
+  if (e0 != cudaSuccess) return map_cuda(e0);
   pp_parser local = S->parser;
   local.tab.partial = last ? 0 : 1;
   local.tab.skip_records = first ? S->parser.tab.skip_records : 0;
@@ -161,6 +167,7 @@ pp_status enqueue_copy_out(pp_streamer* S, int b, const pp_parse_result& r, uint
     return p;
   };
   cudaError_t e = cudaStreamWaitEvent(S->s_d2h, S->parse_done[b], 0);
+  if (e == cudaSuccess) e = cudaEventRecord(S->d2h_start[b], S->s_d2h);
   auto copy = [&](void* dst, const void* src, uint64_t n) {
     if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, S->s_d2h);
   };
@@ -232,6 +239,9 @@ extern "C" void parparaw_stream_destroy(pp_streamer* S) {
     if (S->h2d_done[b]) cudaEventDestroy(S->h2d_done[b]);
     if (S->parse_done[b]) cudaEventDestroy(S->parse_done[b]);
     if (S->d2h_done[b]) cudaEventDestroy(S->d2h_done[b]);
+    if (S->h2d_start[b]) cudaEventDestroy(S->h2d_start[b]);
+    if (S->parse_start[b]) cudaEventDestroy(S->parse_start[b]);
+    if (S->d2h_start[b]) cudaEventDestroy(S->d2h_start[b]);
   }
   if (S->carry_done) cudaEventDestroy(S->carry_done);
   if (S->s_h2d) cudaStreamDestroy(S->s_h2d);
@@ -257,9 +267,9 @@ extern "C" pp_status parparaw_stream_create(const pp_parser* parser, uint64_t pa
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
     e = cudaMalloc(reinterpret_cast<void**>(&S->buf[b]), span);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->h2d_done[b], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->parse_done[b], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->d2h_done[b], cudaEventDisableTiming);
+    for (cudaEvent_t* ev : {&S->h2d_done[b], &S->parse_done[b], &S->d2h_done[b], &S->h2d_start[b],
+                            &S->parse_start[b], &S->d2h_start[b]})
+      if (e == cudaSuccess) e = cudaEventCreate(ev);  // timed: the partitions' device times
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->carry_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_h2d, cudaStreamNonBlocking);
@@ -301,6 +311,19 @@ extern "C" pp_status parparaw_stream_parse(pp_streamer* S, const uint8_t* input,
     if (e == cudaSuccess) e = cudaEventRecord(S->d2h_done[b], S->s_parse);
     if (e == cudaSuccess) e = cudaEventRecord(S->h2d_done[b], S->s_parse);
   }
+  // device times: a partition's copy in and parse are complete when its
+  // result is settled; its copy out when the next partition of the same
+  // set is settled (that parse waits for it), or after the final drain
+  int64_t d2h_pending[2] = {-1, -1};  // the partition whose copy-out time set b still owes
+  auto elapsed = [](cudaEvent_t a, cudaEvent_t z) {
+    float ms = 0.f;
+    return cudaEventElapsedTime(&ms, a, z) == cudaSuccess ? ms : -1.f;
+  };
+  auto take_d2h = [&](int b) {
+    if (d2h_pending[b] >= 0 && cudaEventSynchronize(S->d2h_done[b]) == cudaSuccess)
+      parts[d2h_pending[b]].d2h_ms = elapsed(S->d2h_start[b], S->d2h_done[b]);
+    d2h_pending[b] = -1;
+  };
   if (e == cudaSuccess) e = cudaEventRecord(S->carry_done, S->s_parse);
   if (e != cudaSuccess) return map_cuda(e);
 
@@ -310,6 +333,7 @@ extern "C" pp_status parparaw_stream_parse(pp_streamer* S, const uint8_t* input,
     const int b = static_cast<int>(k % 2);
     const uint64_t lo = k * S->part, ln = std::min(S->part, len - lo);
     cudaError_t r = cudaStreamWaitEvent(S->s_h2d, S->carry_done, 0);
+    if (r == cudaSuccess) r = cudaEventRecord(S->h2d_start[b], S->s_h2d);
     if (r == cudaSuccess && ln > 0)
       r = cudaMemcpyAsync(S->buf[b] + S->carry, input + lo, ln, cudaMemcpyHostToDevice, S->s_h2d);
     if (r == cudaSuccess) r = cudaEventRecord(S->h2d_done[b], S->s_h2d);
@@ -332,6 +356,7 @@ extern "C" pp_status parparaw_stream_parse(pp_streamer* S, const uint8_t* input,
     pp_parse_result r;
     st = settle(S, q.b, q.start, q.length, q.last, q.first, &r);
     if (st != PP_OK) return false;
+    take_d2h(q.b);  // the set's previous partition, copied out before this parse
     if (r.status == PP_E_TIMEOUT || r.status == PP_E_INVALID_INPUT || r.status == PP_E_UNTERMINATED ||
         r.status == PP_OK) {
       const uint64_t need = partition_arena_bytes(P, r);
@@ -344,7 +369,11 @@ extern "C" pp_status parparaw_stream_parse(pp_streamer* S, const uint8_t* input,
       hp.row0 = row0;
       hp.input_offset = q.offset;
       hp.input_bytes = q.length;
+      hp.h2d_ms = elapsed(S->h2d_start[q.b], S->h2d_done[q.b]);
+      hp.parse_ms = elapsed(S->parse_start[q.b], S->parse_done[q.b]);
+      hp.d2h_ms = 0.f;
       if ((st = enqueue_copy_out(S, q.b, r, arena, &used, &hp)) != PP_OK) return false;
+      d2h_pending[q.b] = static_cast<int64_t>(result->num_partitions);
       result->num_partitions += 1;
       result->rows += r.rows;
       result->n_rejected += r.n_rejected;
@@ -402,5 +431,7 @@ extern "C" pp_status parparaw_stream_parse(pp_streamer* S, const uint8_t* input,
     retire(prev, &unused);
   }
   drain(S);
+  take_d2h(0);
+  take_d2h(1);
   return st;
 }

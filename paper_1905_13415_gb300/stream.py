@@ -32,6 +32,9 @@ class Partition:
     nbytes: int                      # input bytes parsed (carry-over included)
     columns: list                    # per column: dict of host tensors (views of the arena)
     row_valid: torch.Tensor
+    h2d_ms: float = 0.0              # device time of the partition's copy in, parse and copy out
+    parse_ms: float = 0.0
+    d2h_ms: float = 0.0
 
 
 class HostArena:
@@ -125,5 +128,5 @@ class StreamParser:
                     col["offsets"] = None
                 cols.append(col)
             out.append(Partition(rows, p.row0, p.input_offset, p.input_bytes, cols,
-                                 arena.view(p.row_valid, nb, torch.uint8)))
+                                 arena.view(p.row_valid, nb, torch.uint8), p.h2d_ms, p.parse_ms, p.d2h_ms))
         return out

@@ -158,6 +158,9 @@ def test_streamed_parse_equals_whole_parse(pp, workload):
     parts = sp.parse(host, HostArena(3 * len(raw) + (1 << 20)) if workload == "mixed" else None)
     assert len(parts) > 3
     assert sum(x.rows for x in parts) == ref.rows
+    # every partition reports the device time of its copy in, parse and copy out
+    for x in parts:
+        assert 0.0 < x.h2d_ms < 1e3 and 0.0 < x.parse_ms < 1e3 and 0.0 < x.d2h_ms < 1e3, x
     for c, col in enumerate(ref.columns):
         if col.offsets is not None:
             fields = []
