@@ -184,3 +184,41 @@ def test_skip_rows_rejects_bad_arguments_without_gpu(abi):
     assert lib.parparaw_skip_rows(fake, 10, None, 3, 10, fake, fake, fake, need, None) == E  # rows missing
     assert lib.parparaw_skip_rows(fake, 100_000, None, 0, 10, fake, fake, fake, need - 1, None) == E  # scratch
     assert lib.parparaw_skip_rows(fake, 10, None, 0, 10, fake, fake, fake + 8, need, None) == E  # misaligned
+
+
+ABI_STRUCTS = ["pp_dfa", "pp_symbol_groups", "pp_schema", "pp_column", "pp_parse_result", "pp_columns",
+               "pp_batch_item", "pp_parser_info", "pp_host_partition", "pp_stream_result", "pp_inference"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Size and field offsets of every struct the binding mirrors, as the C
+    compiler lays them out from include/parparaw.h."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_1905_13415_gb300 import _abi
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "parparaw.h"', "int main(void) {"]
+    for name in ABI_STRUCTS:
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in getattr(_abi, name)._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for name in ABI_STRUCTS:
+        st = getattr(_abi, name)
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert got[(name, field)] == getattr(st, field).offset, (name, field)
