@@ -671,7 +671,8 @@ def main():
     value = whole_job_rate(world, n, step_ms)
     peak, peak_kind = measured_peak_gbs()
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(args.workload, tuned["tile_config"])
+    # the recorded traffic is per launch of the workload's full size
+    traffic = recorded_traffic(args.workload, tuned["tile_config"]) if target == default_n else None
 
     # ------------------------------------------------- end to end (host)
     # Through the library's streaming entry (parparaw_stream_parse): pinned
@@ -767,7 +768,8 @@ def main():
                          "traffic": traffic["bytes_per_launch"] if traffic else None,
                          "traffic_source": (f"ncu DRAM bytes, {traffic['scaled_from']} "
                                             "(profiles/pp_tile_kernel_traffic.txt)") if traffic else
-                                           "no capture of the current kernel sources"},
+                                           ("no capture of the current kernel sources at this tile shape"
+                                            if target == default_n else "recorded for the full size only")},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
